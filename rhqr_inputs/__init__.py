@@ -1,0 +1,66 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+This module holds no arithmetic of the factorisation method: it only draws
+test matrices.  The recipes follow the workloads of the paper's experiments
+(Section 8) as restated for this project:
+
+* ``gaussian``          W with i.i.d. N(0,1) entries.
+* ``spectrum``          W = A diag(sigma) B, A (n x m) and B (m x m) with
+                        orthonormal columns (QR of Gaussian matrices), sigma
+                        log-spaced from 1 down to 1/cond.
+* ``parametric``        the matrix C_m of Section 8, entries
+                        f(x, mu) = sin(10 (mu + x)) / (cos(100 (mu - x)) + 1.1).
+* ``ragged_batch``      the sizes of a batch of tall-skinny problems, n_i
+                        log-uniform in [n_lo, n_hi], m_i drawn from a set.
+
+Each function returns float64 numpy arrays; callers round to the stored dtype.
+GPU-resident variants for the full-size benchmark live in ``device``; they use
+the same recipe with torch's CUDA generator (different values, same law).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+
+def gaussian(n: int, m: int, seed: int) -> np.ndarray:
+    return np.random.default_rng(seed).standard_normal((n, m))
+
+
+def orthonormal(n: int, m: int, rng: np.random.Generator) -> np.ndarray:
+    q, r = np.linalg.qr(rng.standard_normal((n, m)))
+    return q * np.sign(np.diag(r))[None, :]
+
+
+def log_spectrum(m: int, cond: float) -> np.ndarray:
+    return np.logspace(0.0, -np.log10(cond), m)
+
+
+def spectrum(n: int, m: int, cond: float, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    A = orthonormal(n, m, rng)
+    B = orthonormal(m, m, rng)
+    return (A * log_spectrum(m, cond)[None, :]) @ B
+
+
+def parametric(n: int, m: int) -> np.ndarray:
+    x = np.arange(n) / (n - 1)
+    mu = np.arange(m) / max(m - 1, 1)
+    X, MU = np.meshgrid(x, mu, indexing="ij")
+    return np.sin(10.0 * (MU + X)) / (np.cos(100.0 * (MU - X)) + 1.1)
+
+
+def ragged_batch(count: int, n_lo: int, n_hi: int, m_choices, seed: int):
+    rng = np.random.default_rng(seed)
+    n = np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), count)).astype(np.int64)
+    m = rng.choice(np.asarray(m_choices), count)
+    return n, m
+
+
+def to_dtype(W: np.ndarray, dtype: str) -> np.ndarray:
+    """Round a float64 matrix to its stored format (f64 or f32), keep Fortran order."""
+    if dtype == "f64":
+        return np.asfortranarray(W, dtype=np.float64)
+    if dtype == "f32":
+        return np.asfortranarray(W, dtype=np.float32)
+    raise ValueError(dtype)
