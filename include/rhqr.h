@@ -1,0 +1,191 @@
+/*
+ * rhqr.h -- C ABI of the GB300 (sm_103a) randomized Householder QR library.
+ *
+ * Method: L. Grigori, E. Timsit, "Randomized Householder QR" (2024).
+ * A tall-skinny W (n x m, m << n) is factored as W = Q R with
+ *   Q = (I_n - U T (Psi U)^t Psi) [I_m; 0]      (Thm. "mainthm", eq. generalcompact)
+ * where Psi = diag(I_m, Omega) (eq. psi) and Omega is a k x (n-m) sketch
+ * (Gaussian or SRHT, Section 2.3); Psi Q has orthonormal columns.
+ *
+ * Conventions of every entry point
+ *  - Matrices are column-major with a leading dimension (ld >= rows).
+ *  - All data pointers are DEVICE pointers owned by the caller, unless the
+ *    comment says "host".  The library never frees them.
+ *  - Small objects (Z = Psi X, S = Psi U, T, R) are float64.  High-dimensional
+ *    objects (W, U, Q) are float64 or float32 (rhqr_dtype).
+ *  - Work is enqueued on `stream`; a call returns before the GPU finishes.
+ *    Argument errors are returned synchronously.  Conditions found on the GPU
+ *    (breakdown, non-finite data, a bounded wait that ran out) are written to
+ *    the caller's device `rhqr_info` and read after the stream synchronises.
+ *  - No entry point traps, asserts or exits the process.
+ *  - Indices (column numbers in rhqr_info) are 0-based.
+ */
+#ifndef RHQR_H
+#define RHQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (the default stream is NULL). */
+typedef struct CUstream_st *rhqr_stream_t;
+
+typedef enum {
+  RHQR_OK = 0,
+  RHQR_EINVAL = 1,      /* bad argument or shape                              */
+  RHQR_ENOMEM = 2,      /* device allocation failed, or workspace too small    */
+  RHQR_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed         */
+  RHQR_EBREAKDOWN = 4,  /* rho = 0: a column's trailing part lies in Ker(Psi)  */
+  RHQR_ENONFINITE = 5,  /* NaN or Inf met in the small FP64 computations       */
+  RHQR_ETIMEOUT = 6,    /* a bounded device-side wait ran out                  */
+  RHQR_ENOTSUP = 7      /* combination of options not implemented              */
+} rhqr_status;
+
+typedef enum { RHQR_SKETCH_GAUSSIAN = 0, RHQR_SKETCH_SRHT = 1 } rhqr_sketch_kind;
+typedef enum { RHQR_F64 = 0, RHQR_F32 = 1, RHQR_BF16 = 2, RHQR_F16 = 3 } rhqr_dtype;
+typedef enum { RHQR_ALG_LEFT = 0, RHQR_ALG_REC = 1 } rhqr_alg;
+
+/* Opaque, library-owned sketch operator (device arrays inside). */
+typedef struct rhqr_sketch_s *rhqr_sketch;
+
+/* Device-resident result record, written by the kernels of one call. */
+typedef struct {
+  int32_t status;      /* rhqr_status of the device side                     */
+  int32_t column;      /* column of a breakdown / non-finite value, else -1  */
+  int32_t passes_done; /* recRHQR passes completed                           */
+  int32_t reserved;
+} rhqr_info;
+
+/* Options of rhqr_factor.  rhqr_default_opts() fills the defaults. */
+typedef struct {
+  int32_t alg;          /* rhqr_alg (default RHQR_ALG_REC)                         */
+  int32_t passes;       /* recRHQR passes, >= 1: pass i factors the Q of pass i-1
+                           and R = R_p ... R_1 (default 1; ignored for LEFT)       */
+  int32_t limbs_first;  /* 16-bit Gaussian sketch: X is split into this many
+                           bf16/f16 limbs in pass 1 (1..3, default 2)              */
+  int32_t limbs_refine; /* same for passes 2.. (1..3, default 2)                   */
+  int32_t want_U;       /* write U (n x m, W's dtype); default 0                   */
+  int32_t want_Q;       /* write the thin Q (n x m, W's dtype); default 1          */
+  int32_t scaling;      /* reflector scaling of Algorithm 2: 0 = <u_j, e_j> = 1
+                           (default), 1 = ||s_j|| = sqrt 2                         */
+  int32_t reserved;
+  int64_t wait_budget;  /* spin iterations of a device-side wait before it gives up
+                           with RHQR_ETIMEOUT (0 = library default)                */
+} rhqr_opts;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *rhqr_status_string(rhqr_status s);
+
+/* Library version and the compute capability it was built for, e.g. 103. */
+int32_t rhqr_version(void);
+int32_t rhqr_built_arch(void);
+
+void rhqr_default_opts(rhqr_opts *opts /* host */);
+
+/*
+ * rhqr_sketch_create -- draw the sketch Omega_full (k x n) from `seed`
+ * (Section 2.3; the paper leaves the generator open, this library uses the
+ * counter-based SplitMix64 scheme described in the design doc).
+ *   kind = RHQR_SKETCH_SRHT: Omega_full = sqrt(N/k) P H D, N = 2^ceil(log2 n);
+ *          stores N random signs and the k sampled rows (increasing).
+ *   kind = RHQR_SKETCH_GAUSSIAN: Omega_full = G / sqrt(k), G i.i.d. N(0,1)
+ *          (Box-Muller), materialised once in `omega_dtype` (F64, F32, BF16
+ *          or F16) as a k x n row-major array (k*n elements of device memory).
+ * For a factorisation with m columns the sketch used is Psi_m = diag(I_m,
+ * Omega) with Omega = columns m..n-1 of Omega_full (eq. psi).
+ * Requires 1 <= k, k <= N (SRHT), n >= 2.  Allocates device memory (the only
+ * allocating entry points are the *_create ones); the handle is immutable after
+ * creation and may be used from several streams at once.  Synchronises
+ * `stream` before returning.  *out is NULL on error.
+ */
+rhqr_status rhqr_sketch_create(int64_t n, int32_t k, int32_t kind, uint64_t seed,
+                               int32_t omega_dtype, rhqr_stream_t stream, rhqr_sketch *out);
+
+/* Frees the handle's device memory (NULL is accepted). */
+rhqr_status rhqr_sketch_destroy(rhqr_sketch s);
+
+/* Shape of a sketch (host outputs; any may be NULL). */
+rhqr_status rhqr_sketch_shape(rhqr_sketch s, int64_t *n, int32_t *k, int32_t *kind,
+                              int64_t *N, int32_t *omega_dtype);
+
+/*
+ * rhqr_sketch_export -- copy the drawn operator into caller device buffers:
+ *   signs : N int8 values +1/-1 (SRHT only, else ignored; may be NULL)
+ *   rows  : k int32 sampled rows, increasing (SRHT only; may be NULL)
+ *   G     : k x n row-major Gaussian values in omega_dtype, ld = ldg >= n
+ *           (Gaussian only; may be NULL)
+ */
+rhqr_status rhqr_sketch_export(rhqr_sketch s, int8_t *signs, int32_t *rows, void *G,
+                               int64_t ldg, rhqr_stream_t stream);
+
+/*
+ * Workspace sizes (bytes) for rhqr_sketch_apply with c columns of dtype xt, and
+ * for rhqr_factor / rhqr_reconstruct with an n x m matrix of dtype wt.
+ */
+rhqr_status rhqr_sketch_apply_workspace(rhqr_sketch s, int32_t m, int32_t xt, int64_t n,
+                                        int32_t c, size_t *bytes);
+rhqr_status rhqr_workspace_size(rhqr_sketch s, int64_t n, int32_t m, int32_t wt,
+                                const rhqr_opts *opts, size_t *bytes);
+
+/*
+ * rhqr_sketch_apply -- Algorithm 1 (RHSketch): Z = Psi_m X = [X_{1:m}; Omega X_{m+1:n}].
+ *   X : n x c, dtype xt (F64 or F32), leading dimension ldx >= n
+ *   Z : (k+m) x c float64, leading dimension ldz >= k+m (output)
+ * The top m rows are exact copies; the bottom k rows are the sketch.
+ * Requires 0 <= m < n, m <= k.
+ */
+rhqr_status rhqr_sketch_apply(rhqr_sketch s, int32_t m, const void *X, int32_t xt, int64_t n,
+                              int32_t c, int64_t ldx, double *Z, int64_t ldz, void *ws,
+                              size_t ws_bytes, rhqr_stream_t stream);
+
+/*
+ * rhqr_factor -- randomized Householder QR of W (n x m, dtype wt = F64 or F32).
+ *  alg = RHQR_ALG_LEFT: Algorithm 4 (left-looking RHQR): column j is refreshed
+ *        with the previous reflectors, w_j <- w_j - U T^t S^t Psi w_j, sketched,
+ *        and its randomized Householder vector taken (Algorithm 2).
+ *  alg = RHQR_ALG_REC : Algorithm 6 (recRHQR): Z = Psi W, Householder QR of Z
+ *        gives S, T, R, and Q = W R^{-1} (equal to [I;0] - U T U_1^t, Section 3.3)
+ *        is formed by a backward-stable row-wise triangular solve; with
+ *        opts->passes = p > 1 the factorisation is repeated on its own Q and
+ *        R = R_p ... R_1.  U (if wanted) solves W_2 = U_2 ut(T^t S^t Z) of the
+ *        last pass (Algorithm 6, "backward solve").
+ * Outputs (device):
+ *   U  : n x m, dtype wt, ldu >= n   (required for LEFT, optional for REC)
+ *   S  : (k+m) x m float64, lds >= k+m   (= Psi U of the representation)
+ *   T  : m x m float64 (upper triangular, ld = m)
+ *   R  : m x m float64 (upper triangular, ld = m)
+ *   Q  : n x m, dtype wt, ldq >= n   (if opts->want_Q)
+ *   info : device rhqr_info
+ * ws/ws_bytes : device workspace of at least rhqr_workspace_size() bytes.
+ * Requires m >= 1, n > m, k >= m, and for the Gaussian kind a sketch whose
+ * stored n equals this n.  Breakdown (rho = 0) stops the factorisation and
+ * reports the column in info.
+ */
+rhqr_status rhqr_factor(rhqr_sketch s, const void *W, int32_t wt, int64_t n, int32_t m,
+                        int64_t ldw, const rhqr_opts *opts, void *U, int64_t ldu, double *S,
+                        int64_t lds, double *T, double *R, void *Q, int64_t ldq, void *ws,
+                        size_t ws_bytes, rhqr_info *info, rhqr_stream_t stream);
+
+/*
+ * rhqr_reconstruct -- the reconstruction steps of Algorithm 6: given the
+ * Householder QR (S, T, R) of Z = Psi W (S with unit diagonal, Z = (I - S T
+ * S^t)[R; 0]) and W itself, form M = ut(T^t S^t Z), U_1 = S_{1:m},
+ * U_2 = W_2 M^{-1} (column recursion of Section 3.3) and, if Q != NULL,
+ * Q = [I_m; 0] - U T U_1^t (Section 3.2).
+ *   S (lds), Z (ldz): (k+m) x m float64; T, R: m x m float64 (ld = m)
+ *   W: n x m dtype wt (ldw); U: n x m dtype wt (ldu); Q: n x m dtype wt or NULL
+ */
+rhqr_status rhqr_reconstruct(rhqr_sketch s, const double *S, int64_t lds, const double *T,
+                             const double *R, const double *Z, int64_t ldz, const void *W,
+                             int32_t wt, int64_t n, int32_t m, int64_t ldw, void *U, int64_t ldu,
+                             void *Q, int64_t ldq, void *ws, size_t ws_bytes,
+                             rhqr_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RHQR_H */

@@ -1,0 +1,249 @@
+"""Python binding of the GB300 randomized Householder QR library (C ABI in
+``include/rhqr.h``).
+
+This module only marshals arguments: every computation runs in the CUDA
+kernels of ``_build/librhqr.so``.  Functions keep the C names.  Pointer
+arguments accept either an integer device address or a torch tensor (its
+``data_ptr()``); matrices are column-major, i.e. a torch tensor ``X`` of shape
+(rows, cols) with ``X.stride(0) == 1`` and leading dimension ``X.stride(1)``
+(see :func:`colmajor`).  There is no fallback: if the library is missing or
+the GPU call fails, an exception is raised.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import build as _build
+
+F64, F32, BF16, F16 = 0, 1, 2, 3
+GAUSSIAN, SRHT = 0, 1
+ALG_LEFT, ALG_REC = 0, 1
+
+STATUS = {
+    0: "RHQR_OK",
+    1: "RHQR_EINVAL",
+    2: "RHQR_ENOMEM",
+    3: "RHQR_ECUDA",
+    4: "RHQR_EBREAKDOWN",
+    5: "RHQR_ENONFINITE",
+    6: "RHQR_ETIMEOUT",
+    7: "RHQR_ENOTSUP",
+}
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "rhqr.h")
+
+
+class RHQRError(RuntimeError):
+    def __init__(self, func: str, code: int):
+        self.code = code
+        super().__init__(f"{func} failed: {STATUS.get(code, code)}")
+
+
+class rhqr_opts(ctypes.Structure):
+    _fields_ = [
+        ("alg", ctypes.c_int32),
+        ("passes", ctypes.c_int32),
+        ("limbs_first", ctypes.c_int32),
+        ("limbs_refine", ctypes.c_int32),
+        ("want_U", ctypes.c_int32),
+        ("want_Q", ctypes.c_int32),
+        ("scaling", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("wait_budget", ctypes.c_int64),
+    ]
+
+
+class rhqr_info(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32),
+        ("column", ctypes.c_int32),
+        ("passes_done", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+_lib = None
+_p = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+_sz = ctypes.c_size_t
+
+_SIGNATURES = {
+    "rhqr_status_string": (ctypes.c_char_p, [_i32]),
+    "rhqr_version": (_i32, []),
+    "rhqr_built_arch": (_i32, []),
+    "rhqr_default_opts": (None, [ctypes.POINTER(rhqr_opts)]),
+    "rhqr_sketch_create": (_i32, [_i64, _i32, _i32, _u64, _i32, _p, ctypes.POINTER(_p)]),
+    "rhqr_sketch_destroy": (_i32, [_p]),
+    "rhqr_sketch_shape": (_i32, [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                 ctypes.POINTER(_i64), ctypes.POINTER(_i32)]),
+    "rhqr_sketch_export": (_i32, [_p, _p, _p, _p, _i64, _p]),
+    "rhqr_sketch_apply_workspace": (_i32, [_p, _i32, _i32, _i64, _i32, ctypes.POINTER(_sz)]),
+    "rhqr_workspace_size": (_i32, [_p, _i64, _i32, _i32, ctypes.POINTER(rhqr_opts), ctypes.POINTER(_sz)]),
+    "rhqr_sketch_apply": (_i32, [_p, _i32, _p, _i32, _i64, _i32, _i64, _p, _i64, _p, _sz, _p]),
+    "rhqr_factor": (_i32, [_p, _p, _i32, _i64, _i32, _i64, ctypes.POINTER(rhqr_opts), _p, _i64, _p, _i64, _p, _p,
+                           _p, _i64, _p, _sz, _p, _p]),
+    "rhqr_reconstruct": (_i32, [_p, _p, _i64, _p, _p, _p, _i64, _p, _i32, _i64, _i32, _i64, _p, _i64, _p, _i64, _p,
+                                _sz, _p]),
+}
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/rhqr.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rhqr_[a-z0-9_]+)\s*\(", text)))
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it first if needed) and bind the ABI."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError("CUDA library not built: call paper_2405_10923_gb300.build.build()")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in _SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(name, code):
+    if code != 0:
+        raise RHQRError(name, code)
+
+
+def colmajor(t, ld: int | None = None):
+    """A column-major (Fortran-order) copy of a 2-D torch tensor, ld >= rows."""
+    import torch
+
+    rows, cols = t.shape
+    ld = rows if ld is None else ld
+    buf = torch.zeros((cols, ld), dtype=t.dtype, device=t.device)
+    out = buf.t()[:rows]
+    out.copy_(t)
+    return out
+
+
+def ld_of(t) -> int:
+    if t.dim() != 2 or t.stride(0) != 1:
+        raise ValueError("expected a column-major 2-D tensor (stride(0) == 1)")
+    return max(t.stride(1), t.shape[0])
+
+
+def dtype_code(t) -> int:
+    import torch
+
+    return {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}[t.dtype]
+
+
+# ---------------------------------------------------------------------------
+# the C entry points, same names
+# ---------------------------------------------------------------------------
+
+
+def rhqr_status_string(code: int) -> str:
+    return load().rhqr_status_string(code).decode()
+
+
+def rhqr_version() -> int:
+    return load().rhqr_version()
+
+
+def rhqr_built_arch() -> int:
+    return load().rhqr_built_arch()
+
+
+def rhqr_default_opts() -> rhqr_opts:
+    o = rhqr_opts()
+    load().rhqr_default_opts(ctypes.byref(o))
+    return o
+
+
+def rhqr_sketch_create(n: int, k: int, kind: int, seed: int, omega_dtype: int = F64, stream=None) -> int:
+    out = _p()
+    _check("rhqr_sketch_create",
+           load().rhqr_sketch_create(n, k, kind, seed & ((1 << 64) - 1), omega_dtype, _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def rhqr_sketch_destroy(s: int) -> None:
+    _check("rhqr_sketch_destroy", load().rhqr_sketch_destroy(s))
+
+
+def rhqr_sketch_shape(s: int):
+    n, k, kind, N, dt = _i64(), _i32(), _i32(), _i64(), _i32()
+    _check("rhqr_sketch_shape", load().rhqr_sketch_shape(s, ctypes.byref(n), ctypes.byref(k), ctypes.byref(kind),
+                                                         ctypes.byref(N), ctypes.byref(dt)))
+    return n.value, k.value, kind.value, N.value, dt.value
+
+
+def rhqr_sketch_export(s: int, signs=None, rows=None, G=None, ldg: int = 0, stream=None) -> None:
+    _check("rhqr_sketch_export", load().rhqr_sketch_export(s, _ptr(signs), _ptr(rows), _ptr(G), ldg, _stream(stream)))
+
+
+def rhqr_sketch_apply_workspace(s: int, m: int, xt: int, n: int, c: int) -> int:
+    b = _sz()
+    _check("rhqr_sketch_apply_workspace", load().rhqr_sketch_apply_workspace(s, m, xt, n, c, ctypes.byref(b)))
+    return b.value
+
+
+def rhqr_workspace_size(s: int, n: int, m: int, wt: int, opts: rhqr_opts | None = None) -> int:
+    b = _sz()
+    _check("rhqr_workspace_size", load().rhqr_workspace_size(s, n, m, wt, ctypes.byref(opts) if opts else None,
+                                                             ctypes.byref(b)))
+    return b.value
+
+
+def rhqr_sketch_apply(s, m, X, xt, n, c, ldx, Z, ldz, ws, ws_bytes, stream=None) -> None:
+    _check("rhqr_sketch_apply", load().rhqr_sketch_apply(s, m, _ptr(X), xt, n, c, ldx, _ptr(Z), ldz, _ptr(ws),
+                                                         ws_bytes, _stream(stream)))
+
+
+def rhqr_factor(s, W, wt, n, m, ldw, opts, U, ldu, S, lds, T, R, Q, ldq, ws, ws_bytes, info, stream=None) -> None:
+    _check("rhqr_factor", load().rhqr_factor(s, _ptr(W), wt, n, m, ldw, ctypes.byref(opts) if opts else None, _ptr(U),
+                                             ldu, _ptr(S), lds, _ptr(T), _ptr(R), _ptr(Q), ldq, _ptr(ws), ws_bytes,
+                                             _ptr(info), _stream(stream)))
+
+
+def rhqr_reconstruct(s, S, lds, T, R, Z, ldz, W, wt, n, m, ldw, U, ldu, Q, ldq, ws, ws_bytes, stream=None) -> None:
+    _check("rhqr_reconstruct", load().rhqr_reconstruct(s, _ptr(S), lds, _ptr(T), _ptr(R), _ptr(Z), ldz, _ptr(W), wt, n,
+                                                       m, ldw, _ptr(U), ldu, _ptr(Q), ldq, _ptr(ws), ws_bytes,
+                                                       _stream(stream)))
+
+
+def read_info(info_tensor) -> dict:
+    """Decode a 4-int32 device tensor holding an rhqr_info (synchronises)."""
+    v = info_tensor.cpu().tolist()
+    return {"status": int(v[0]), "column": int(v[1]), "passes_done": int(v[2])}

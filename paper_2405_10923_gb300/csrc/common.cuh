@@ -1,0 +1,161 @@
+// Shared definitions of the CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/rhqr.h"
+
+namespace rhqr {
+
+// Launch/runtime error -> RHQR_ECUDA (synchronous part of the contract).
+#define RHQR_CUDA_TRY(expr)                                    \
+  do {                                                         \
+    cudaError_t e_ = (expr);                                   \
+    if (e_ != cudaSuccess) {                                   \
+      (void)cudaGetLastError();                                \
+      return RHQR_ECUDA;                                       \
+    }                                                          \
+  } while (0)
+
+#define RHQR_TRY(expr)                 \
+  do {                                 \
+    rhqr_status s_ = (expr);           \
+    if (s_ != RHQR_OK) return s_;      \
+  } while (0)
+
+#define RHQR_LAUNCH_CHECK() RHQR_CUDA_TRY(cudaGetLastError())
+
+inline size_t dtype_size(int32_t t) {
+  switch (t) {
+    case RHQR_F64: return 8;
+    case RHQR_F32: return 4;
+    case RHQR_BF16:
+    case RHQR_F16: return 2;
+    default: return 0;
+  }
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Bump allocator over a caller-provided workspace.
+struct Carver {
+  char *base;
+  size_t cap, off;
+  Carver(void *p, size_t c) : base((char *)p), cap(c), off(0) {}
+  template <class T>
+  T *take(size_t count) {
+    off = align_up(off, 256);
+    size_t bytes = count * sizeof(T);
+    if (base == nullptr) {  // sizing pass
+      off += bytes;
+      return nullptr;
+    }
+    if (off + bytes > cap) {
+      off = cap + 1;
+      return nullptr;
+    }
+    T *p = (T *)(base + off);
+    off += bytes;
+    return p;
+  }
+  bool overflow() const { return base != nullptr && off > cap; }
+  size_t used() const { return off; }
+};
+
+// ----------------------------------------------------------------------------
+// device helpers
+// ----------------------------------------------------------------------------
+
+template <class T>
+__device__ __forceinline__ double to_f64(T v);
+template <>
+__device__ __forceinline__ double to_f64<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ double to_f64<float>(float v) { return (double)v; }
+
+template <>
+__device__ __forceinline__ double to_f64<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+template <>
+__device__ __forceinline__ double to_f64<__half>(__half v) { return (double)__half2float(v); }
+
+template <class T>
+__device__ __forceinline__ T from_f64(double v);
+template <>
+__device__ __forceinline__ double from_f64<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float from_f64<float>(double v) { return (float)v; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum (fixed order: lane tree, then warp tree).  `red` holds >= 32
+// doubles of shared memory.  Every thread gets the result.
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = (threadIdx.x < (unsigned)nw) ? red[threadIdx.x] : 0.0;
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Record a device-side condition in the caller's info (first writer wins).
+__device__ __forceinline__ void set_status(rhqr_info *info, int32_t st, int32_t col) {
+  if (info == nullptr) return;
+  if (atomicCAS(&info->status, (int)RHQR_OK, st) == RHQR_OK) info->column = col;
+}
+
+// Grid-wide barrier for cooperative launches, with a bounded wait.
+// `bar[0]` counts arrivals, `bar[1]` is the generation.  Returns false (and
+// records RHQR_ETIMEOUT) if the wait ran out; every block then stops.
+__device__ __forceinline__ bool grid_barrier(unsigned int *bar, long long budget, rhqr_info *info,
+                                             volatile int *abort_flag) {
+  __syncthreads();
+  __shared__ int ok_s;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int *vgen = bar + 1;
+    unsigned int gen = *vgen;
+    __threadfence();
+    unsigned int arrived = atomicAdd(bar, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (*vgen == gen) {
+        if (*abort_flag) { ok = 0; break; }
+        if (++it > budget) {
+          ok = 0;
+          *abort_flag = 1;
+          set_status(info, RHQR_ETIMEOUT, -1);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+}  // namespace rhqr

@@ -1,0 +1,381 @@
+// Left-looking RHQR (Algorithm 4) on the GPU.
+//
+// The raw sketches z_j = Psi w_j of all columns are formed once up front (the
+// sketch of column j taken at the start of step j only depends on the
+// untouched input column).  Step j then runs:
+//   1. c = T_j^t (S_j^t z_j)                               (small, float64)
+//   2. column kernel: w_j <- w_j - U_{:, <j} c over all n rows, written to
+//      U[:, j]; the previous column's deferred scale u_{j-1} = u~_{j-1}/gamma
+//      is applied while it is read (and written back); the refreshed column
+//      is sketched in the same pass (SRHT stage A on the block's rows, or the
+//      Gaussian partial products); rows < m are copied into y exactly
+//   3. y = Psi w_j (SRHT stage B / ordered reduction of Gaussian partials)
+//   4. RHVector (Algorithm 2) on (w_j, y): sigma, rho, gamma, beta, s_j, r_j
+//   5. t_j = (-beta T_j S_j^t s_j; beta) and the next step's coefficients.
+#include "apply.cuh"
+#include "common.cuh"
+#include "left.cuh"
+#include "small.cuh"
+
+namespace rhqr {
+
+// ---------------------------------------------------------------------------
+// step 1 / 5 helpers
+// dots: for l < nd: d[l] = S[:, l] . s_j  (if dst_d), v[l] = S[:, l] . z  (l < nv)
+// ---------------------------------------------------------------------------
+__global__ void left_dots_kernel(const double *S, int64_t lds, int64_t p, int32_t j, int32_t nd, const double *z,
+                                 int32_t nv, double *d, double *v) {
+  __shared__ double red[32];
+  int l = blockIdx.x;
+  int which = blockIdx.y;  // 0: d (against s_j), 1: v (against z)
+  if ((which == 0 && l >= nd) || (which == 1 && l >= nv)) return;
+  const double *a = S + (int64_t)l * lds;
+  const double *b = (which == 0) ? S + (int64_t)j * lds : z;
+  int64_t start = (which == 0) ? j : l;  // s_j vanishes above j, s_l above l
+  double acc = 0.0;
+  for (int64_t r = start + threadIdx.x; r < p; r += blockDim.x) acc += a[r] * b[r];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    if (which == 0) d[l] = acc;
+    else v[l] = acc;
+  }
+}
+
+// T[:, j] from d (if j >= 0 and finishing column j), then c = T_{nc}^t v (nc values)
+__global__ void left_tcol_coef_kernel(double *T, int32_t m, int32_t j, const double *beta, const double *d,
+                                      const double *v, int32_t nc, double *c) {
+  if (j >= 0) {
+    double bj = beta[j];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      double val = 0.0;
+      if (i < j) {
+        for (int l = i; l < j; ++l) val += T[(int64_t)l * m + i] * d[l];
+        val = -bj * val;
+      } else if (i == j) {
+        val = bj;
+      }
+      T[(int64_t)j * m + i] = val;
+    }
+    __syncthreads();
+  }
+  for (int l = threadIdx.x; l < nc; l += blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i <= l; ++i) acc += T[(int64_t)l * m + i] * v[i];
+    c[l] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// step 2: column kernels
+// ---------------------------------------------------------------------------
+struct ColArgs {
+  const void *W;
+  int64_t ldw;
+  void *U;
+  int64_t ldu;
+  int64_t n;
+  int32_t m, j;
+  const double *c;      // j coefficients
+  const double *gamma;  // gamma[j-1] scales column j-1
+  double *y;            // (k+m) sketch, rows < m written here
+  int32_t unit;         // unit-diagonal scaling: u_jj = 1 exactly
+};
+
+template <class T>
+__device__ __forceinline__ T refresh_row(const ColArgs &a, int64_t i, const double *c_s, T inv_g) {
+  const T *W = (const T *)a.W;
+  T *U = (T *)a.U;
+  T w = W[(int64_t)a.j * a.ldw + i];
+  const int j = a.j;
+  // previous columns, the last one still unscaled
+  for (int l = 0; l + 1 < j; ++l) w -= U[(int64_t)l * a.ldu + i] * (T)c_s[l];
+  if (j >= 1) {
+    T *up = U + (int64_t)(j - 1) * a.ldu + i;
+    T u = (i < j - 1) ? T(0) : ((i == j - 1 && a.unit) ? T(1) : *up * inv_g);
+    *up = u;
+    w -= u * (T)c_s[j - 1];
+  }
+  U[(int64_t)j * a.ldu + i] = w;
+  return w;
+}
+
+// SRHT: block j1 owns rows [j1 N2, (j1+1) N2); refresh, signs, FWHT, keep samples
+template <class T>
+__global__ void left_column_srht_kernel(ColArgs a, const uint32_t *sign_bits, int32_t N2, const int32_t *i2_list,
+                                        int32_t d2, T *Ystage) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *v = reinterpret_cast<T *>(smem_raw);
+  __shared__ double c_s[1024];
+  for (int l = threadIdx.x; l < a.j; l += blockDim.x) c_s[l] = a.c[l];
+  const T inv_g = (a.j >= 1) ? (T)(1.0 / a.gamma[a.j - 1]) : T(1);
+  __syncthreads();
+  const int64_t row0 = (int64_t)blockIdx.x * N2;
+  for (int t = threadIdx.x; t < N2; t += blockDim.x) {
+    int64_t i = row0 + t;
+    T val = T(0);
+    if (i < a.n) {
+      T w = refresh_row<T>(a, i, c_s, inv_g);
+      if (i < a.m) {
+        a.y[i] = (double)w;
+      } else {
+        val = ((sign_bits[i >> 5] >> (i & 31)) & 1u) ? -w : w;
+      }
+    }
+    v[t] = val;
+  }
+  __syncthreads();
+  for (int h = 1; h < N2; h <<= 1) {
+    for (int t = threadIdx.x; t < (N2 >> 1); t += blockDim.x) {
+      int i = (t / h) * (2 * h) + (t % h);
+      T x0 = v[i], x1 = v[i + h];
+      v[i] = x0 + x1;
+      v[i + h] = x0 - x1;
+    }
+    __syncthreads();
+  }
+  T *ys = Ystage + (int64_t)blockIdx.x * d2;
+  for (int s = threadIdx.x; s < d2; s += blockDim.x) ys[s] = v[i2_list[s]];
+}
+
+template <class T>
+__global__ void left_srht_combine_kernel(const T *Ystage, int32_t N1, int32_t d2, const int32_t *sample_i1,
+                                         const int32_t *sample_slot, int32_t k, int32_t m, double scale, double *y) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k) return;
+  int i1 = sample_i1[r], slot = sample_slot[r];
+  double acc = 0.0;
+  for (int j1 = 0; j1 < N1; ++j1) {
+    double t = (double)Ystage[(int64_t)j1 * d2 + slot];
+    acc += (__popc(i1 & j1) & 1) ? -t : t;
+  }
+  y[m + r] = acc * scale;
+}
+
+// Gaussian: block owns rows [b*RB, (b+1)*RB); partial[b][r] = sum_i G[r, i] w_i over rows i >= m
+constexpr int LG_RB = 256;
+template <class T, class TG>
+__global__ void __launch_bounds__(LG_RB) left_column_gauss_kernel(ColArgs a, const TG *G, int64_t ldg, int32_t k,
+                                                                  double *part) {
+  __shared__ double w_s[LG_RB];
+  __shared__ double c_s[1024];
+  for (int l = threadIdx.x; l < a.j; l += blockDim.x) c_s[l] = a.c[l];
+  const T inv_g = (a.j >= 1) ? (T)(1.0 / a.gamma[a.j - 1]) : T(1);
+  __syncthreads();
+  const int64_t row0 = (int64_t)blockIdx.x * LG_RB;
+  int64_t i = row0 + threadIdx.x;
+  double wd = 0.0;
+  if (i < a.n) {
+    T w = refresh_row<T>(a, i, c_s, inv_g);
+    if (i < a.m) a.y[i] = (double)w;
+    else wd = (double)w;
+  }
+  w_s[threadIdx.x] = wd;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = LG_RB / 32;
+  const int64_t rows = min((int64_t)LG_RB, a.n - row0);
+  for (int r = wid; r < k; r += nw) {
+    double acc = 0.0;
+    for (int t = lane; t < rows; t += 32) acc += to_f64<TG>(G[(int64_t)r * ldg + row0 + t]) * w_s[t];
+    acc = warp_sum(acc);
+    if (lane == 0) part[(int64_t)blockIdx.x * k + r] = acc;
+  }
+}
+
+__global__ void left_gauss_reduce_kernel(const double *part, int32_t nb, int32_t k, int32_t m, double scale,
+                                         double *y) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k) return;
+  double acc = 0.0;
+  for (int b = 0; b < nb; ++b) acc += part[(int64_t)b * k + r];
+  y[m + r] = acc * scale;
+}
+
+// ---------------------------------------------------------------------------
+// step 4: RHVector on y (Algorithm 2), one block
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void left_rhvector_kernel(const double *y, int64_t p, int32_t m, int32_t j, int32_t scaling, double *S,
+                                     int64_t lds, double *R, double *beta, double *gamma_out, T *U, int64_t ldu,
+                                     rhqr_info *info, int *stop) {
+  __shared__ double red[32];
+  if (*stop) return;
+  double s = 0.0;
+  for (int64_t r = j + threadIdx.x; r < p; r += blockDim.x) s += y[r] * y[r];
+  s = block_sum(s, red);
+  const double rho = sqrt(s);
+  const double a = y[j];
+  if (!isfinite(rho) || !isfinite(a)) {
+    if (threadIdx.x == 0) { set_status(info, RHQR_ENONFINITE, j); *stop = 1; }
+    return;
+  }
+  if (rho == 0.0) {
+    if (threadIdx.x == 0) { set_status(info, RHQR_EBREAKDOWN, j); *stop = 1; }
+    return;
+  }
+  const double sigma = a < 0.0 ? -1.0 : 1.0;
+  const double g = a + sigma * rho;
+  const double div = (scaling == 0) ? g : sqrt(rho * (rho + fabs(a)));
+  for (int64_t r = threadIdx.x; r < p; r += blockDim.x) {
+    double v = 0.0;
+    if (r == j) v = g / div;
+    else if (r > j) v = y[r] / div;
+    S[(int64_t)j * lds + r] = v;
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double rv = 0.0;
+    if (i < j) rv = y[i];
+    else if (i == j) rv = -sigma * rho;
+    R[(int64_t)j * m + i] = rv;
+    // top rows of the stored vector: zero above j, gamma (unscaled) at j
+    if (i < j) U[(int64_t)j * ldu + i] = T(0);
+    else if (i == j) U[(int64_t)j * ldu + i] = (T)g;
+  }
+  if (threadIdx.x == 0) {
+    beta[j] = (scaling == 0) ? 1.0 + fabs(a) / rho : 1.0;
+    gamma_out[j] = div;
+  }
+}
+
+// final deferred scale of column j: u = u~ / gamma (rows >= j+1), u_j = 1 (or gamma/div)
+template <class T>
+__global__ void left_scale_last_kernel(T *U, int64_t ldu, int64_t n, int32_t j, const double *gamma, int32_t unit) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T *up = U + (int64_t)j * ldu + i;
+  T inv_g = (T)(1.0 / gamma[j]);
+  *up = (i < j) ? T(0) : ((i == j && unit) ? T(1) : *up * inv_g);
+}
+
+// ---------------------------------------------------------------------------
+// host
+// ---------------------------------------------------------------------------
+
+size_t left_workspace_bytes(const SketchView &s, int64_t n, int32_t m, int32_t wt) {
+  Carver c(nullptr, 0);
+  int64_t p = (int64_t)s.k + m;
+  c.take<double>((size_t)p * m);  // Zraw
+  c.take<double>(p);              // y
+  c.take<double>(4 * (size_t)m);  // c, v, d, gamma
+  c.take<double>(m);              // beta
+  c.take<int>(4);                 // stop flag
+  c.take<double>((size_t)m * m);  // G = T U_1^t
+  c.take<char>(small_padded_bytes(m));
+  if (s.kind == RHQR_SKETCH_SRHT) c.take<char>((size_t)s.N1 * s.d2 * dtype_size(wt));
+  else c.take<double>((size_t)ceil_div(n, LG_RB) * s.k);
+  size_t apply_ws = sketch_apply_workspace_bytes(s, m, wt, n, m);
+  return c.used() + align_up(apply_ws, 256) + 1024;
+}
+
+template <class T>
+static rhqr_status left_typed(const SketchView &s, const T *W, int64_t n, int32_t m, int64_t ldw, int32_t scaling,
+                              T *U, int64_t ldu, double *S, int64_t lds, double *Tm, double *R, T *Q, int64_t ldq,
+                              void *ws, size_t ws_bytes, rhqr_info *info, cudaStream_t st) {
+  const int64_t p = (int64_t)s.k + m;
+  Carver cv(ws, ws_bytes);
+  double *Zraw = cv.take<double>((size_t)p * m);
+  double *y = cv.take<double>(p);
+  double *cbuf = cv.take<double>(m);
+  double *vbuf = cv.take<double>(m);
+  double *dbuf = cv.take<double>(m);
+  double *gam = cv.take<double>(m);
+  double *beta = cv.take<double>(m);
+  int *stop = cv.take<int>(4);
+  double *Gm = cv.take<double>((size_t)m * m);
+  char *GT = cv.take<char>(small_padded_bytes(m));
+  void *stage = nullptr;
+  if (s.kind == RHQR_SKETCH_SRHT) stage = cv.take<char>((size_t)s.N1 * s.d2 * sizeof(T));
+  else stage = cv.take<double>((size_t)ceil_div(n, LG_RB) * s.k);
+  size_t apply_ws = sketch_apply_workspace_bytes(s, m, sizeof(T) == 8 ? RHQR_F64 : RHQR_F32, n, m);
+  char *aws = cv.take<char>(apply_ws);
+  if (cv.overflow()) return RHQR_ENOMEM;
+  if (m > 1024) return RHQR_ENOTSUP;
+
+  RHQR_CUDA_TRY(cudaMemsetAsync(stop, 0, 4 * sizeof(int), st));
+  RHQR_CUDA_TRY(cudaMemsetAsync(Tm, 0, sizeof(double) * m * m, st));
+  // raw sketches of all columns (Algorithm 4 sketches w_j before refreshing it)
+  RHQR_TRY(sketch_apply_simt(s, m, W, sizeof(T) == 8 ? RHQR_F64 : RHQR_F32, n, m, ldw, Zraw, p, aws, apply_ws, st));
+
+  ColArgs ca{W, ldw, U, ldu, n, m, 0, cbuf, gam, y, scaling == 0 ? 1 : 0};
+  const double scale = 1.0 / sqrt((double)s.k);
+  for (int j = 0; j < m; ++j) {
+    if (j >= 1) {
+      // d_l = s_l . s_{j-1} (l < j-1) finishes column j-1 of T; v_l = s_l . z_j (l < j)
+      dim3 g((unsigned)j, 2);
+      left_dots_kernel<<<g, 256, 0, st>>>(S, lds, p, j - 1, j - 1, Zraw + (int64_t)j * p, j, dbuf, vbuf);
+      RHQR_LAUNCH_CHECK();
+      left_tcol_coef_kernel<<<1, 256, 0, st>>>(Tm, m, j - 1, beta, dbuf, vbuf, j, cbuf);
+      RHQR_LAUNCH_CHECK();
+    }
+    ca.j = j;
+    if (s.kind == RHQR_SKETCH_SRHT) {
+      size_t smem = (size_t)s.N2 * sizeof(T);
+      if (smem > 48 * 1024)
+        RHQR_CUDA_TRY(cudaFuncSetAttribute(left_column_srht_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+      left_column_srht_kernel<T><<<s.N1, 512, smem, st>>>(ca, s.sign_bits, s.N2, s.i2_list, s.d2, (T *)stage);
+      RHQR_LAUNCH_CHECK();
+      left_srht_combine_kernel<T><<<(unsigned)ceil_div(s.k, 128), 128, 0, st>>>(
+          (const T *)stage, s.N1, s.d2, s.sample_i1, s.sample_slot, s.k, m, scale, y);
+      RHQR_LAUNCH_CHECK();
+    } else {
+      int nb = (int)ceil_div(n, LG_RB);
+      switch (s.omega_dtype) {
+        case RHQR_F64:
+          left_column_gauss_kernel<T, double><<<nb, LG_RB, 0, st>>>(ca, (const double *)s.G, s.ldg, s.k,
+                                                                    (double *)stage);
+          break;
+        case RHQR_F32:
+          left_column_gauss_kernel<T, float><<<nb, LG_RB, 0, st>>>(ca, (const float *)s.G, s.ldg, s.k,
+                                                                   (double *)stage);
+          break;
+        case RHQR_BF16:
+          left_column_gauss_kernel<T, __nv_bfloat16><<<nb, LG_RB, 0, st>>>(ca, (const __nv_bfloat16 *)s.G, s.ldg,
+                                                                           s.k, (double *)stage);
+          break;
+        case RHQR_F16:
+          left_column_gauss_kernel<T, __half><<<nb, LG_RB, 0, st>>>(ca, (const __half *)s.G, s.ldg, s.k,
+                                                                    (double *)stage);
+          break;
+        default:
+          return RHQR_EINVAL;
+      }
+      RHQR_LAUNCH_CHECK();
+      left_gauss_reduce_kernel<<<(unsigned)ceil_div(s.k, 128), 128, 0, st>>>((const double *)stage, nb, s.k, m,
+                                                                             scale, y);
+      RHQR_LAUNCH_CHECK();
+    }
+    left_rhvector_kernel<T><<<1, 256, 0, st>>>(y, p, m, j, scaling, S, lds, R, beta, gam, U, ldu, info, stop);
+    RHQR_LAUNCH_CHECK();
+  }
+  // finish T's last column and the last column's scale
+  {
+    dim3 g((unsigned)std::max(1, m - 1), 2);
+    left_dots_kernel<<<g, 256, 0, st>>>(S, lds, p, m - 1, m - 1, Zraw, 0, dbuf, vbuf);
+    RHQR_LAUNCH_CHECK();
+    left_tcol_coef_kernel<<<1, 256, 0, st>>>(Tm, m, m - 1, beta, dbuf, vbuf, 0, cbuf);
+    RHQR_LAUNCH_CHECK();
+    left_scale_last_kernel<T><<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(U, ldu, n, m - 1, gam, scaling == 0);
+    RHQR_LAUNCH_CHECK();
+  }
+  if (Q != nullptr) {
+    // Q = [I; 0] - U (T U_1^t)  (Section 3.2)
+    RHQR_TRY(t_u1t(Tm, S, lds, m, Gm, st));
+    RHQR_TRY(pad_transpose<T>(Gm, m, 1, (T *)GT, st));
+    RHQR_TRY(rows_form_q<T>(U, ldu, 0, n, m, (const T *)GT, Q, ldq, st));
+  }
+  return RHQR_OK;
+}
+
+rhqr_status left_factor(const SketchView &s, const void *W, int32_t wt, int64_t n, int32_t m, int64_t ldw,
+                        int32_t scaling, void *U, int64_t ldu, double *S, int64_t lds, double *T, double *R, void *Q,
+                        int64_t ldq, void *ws, size_t ws_bytes, rhqr_info *info, cudaStream_t st) {
+  if (wt == RHQR_F64)
+    return left_typed<double>(s, (const double *)W, n, m, ldw, scaling, (double *)U, ldu, S, lds, T, R,
+                              (double *)Q, ldq, ws, ws_bytes, info, st);
+  if (wt == RHQR_F32)
+    return left_typed<float>(s, (const float *)W, n, m, ldw, scaling, (float *)U, ldu, S, lds, T, R, (float *)Q,
+                             ldq, ws, ws_bytes, info, st);
+  return RHQR_ENOTSUP;
+}
+
+}  // namespace rhqr

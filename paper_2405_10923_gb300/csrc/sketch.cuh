@@ -1,0 +1,30 @@
+// Device-side view of a sketch handle and the RHSketch launchers.
+#pragma once
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace rhqr {
+
+struct SketchView {
+  int64_t n, N;
+  int32_t k, kind, omega_dtype;
+  // SRHT: sign bits, sampled rows and their Kronecker split N = N1 * N2
+  const uint32_t *sign_bits;
+  const int32_t *rows;
+  int32_t N1, N2, d2;          // d2 distinct in-block positions of the sampled rows
+  const int32_t *i2_list;      // d2 positions, increasing
+  const int32_t *sample_i1;    // k block indices
+  const int32_t *sample_slot;  // k slots into i2_list
+  // Gaussian: k x n row-major values (ld = ldg) in omega_dtype
+  const void *G;
+  int64_t ldg;
+};
+
+size_t sketch_apply_workspace_bytes(const SketchView &s, int32_t m, int32_t xt, int64_t n, int32_t c);
+
+// Z = Psi_m X with the SIMT kernels (SRHT or Gaussian of any stored dtype).
+rhqr_status sketch_apply_simt(const SketchView &s, int32_t m, const void *X, int32_t xt, int64_t n, int32_t c,
+                              int64_t ldx, double *Z, int64_t ldz, void *ws, size_t ws_bytes, cudaStream_t st);
+
+}  // namespace rhqr

@@ -1,0 +1,28 @@
+// Host launchers of the small FP64 kernels (small.cu).
+#pragma once
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace rhqr {
+
+size_t hqr_workspace_bytes(int64_t p, int32_t m);
+
+// Householder QR of Z (p x m, ldz): S (p x m, lds), R (m x m), beta (m).
+rhqr_status householder_qr_small(const double *Z, int64_t ldz, int64_t p, int32_t m, double *S, int64_t lds,
+                                 double *R, double *beta, int32_t scaling, void *ws, size_t ws_bytes,
+                                 rhqr_info *info, long long budget, cudaStream_t st);
+
+// T from S and beta (eq. generalwoodburry); SS: m*m doubles of scratch.
+rhqr_status t_factor_small(const double *S, int64_t lds, int64_t p, int32_t m, const double *beta, double *SS,
+                           double *T, cudaStream_t st);
+
+rhqr_status triu_mul(const double *A, const double *B, int32_t m, double *C, cudaStream_t st);
+rhqr_status t_u1t(const double *T, const double *S, int64_t lds, int32_t m, double *Gm, cudaStream_t st);
+rhqr_status m_factor(const double *T, const double *S, int64_t lds, const double *Z, int64_t ldz, int64_t p,
+                     int32_t m, double *StZ, double *M, cudaStream_t st);
+rhqr_status cast_f32(const double *A, int64_t n, float *B, cudaStream_t st);
+rhqr_status copy_f64(const double *A, int64_t n, double *B, cudaStream_t st);
+rhqr_status info_passes(rhqr_info *info, int32_t passes, cudaStream_t st);
+
+}  // namespace rhqr

@@ -1,0 +1,114 @@
+"""Torch-tensor conveniences over the C ABI: they allocate outputs and the
+workspace with torch and call the entry points of ``include/rhqr.h``.  No
+arithmetic of the method happens here."""
+
+from __future__ import annotations
+
+import torch
+
+from . import (ALG_LEFT, ALG_REC, BF16, F16, F32, F64, GAUSSIAN, SRHT, colmajor, dtype_code, ld_of, read_info,
+               rhqr_default_opts, rhqr_factor, rhqr_reconstruct, rhqr_sketch_apply, rhqr_sketch_apply_workspace,
+               rhqr_sketch_create, rhqr_sketch_destroy, rhqr_sketch_export, rhqr_sketch_shape, rhqr_workspace_size)
+
+TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}
+__all__ = ["Sketch", "factor", "reconstruct", "colmajor", "ALG_LEFT", "ALG_REC", "GAUSSIAN", "SRHT"]
+
+
+class Sketch:
+    """Owner of an rhqr_sketch handle."""
+
+    def __init__(self, n: int, k: int, kind: int, seed: int, omega_dtype: int = F64, stream=None):
+        self.handle = rhqr_sketch_create(n, k, kind, seed, omega_dtype, stream)
+        self.n, self.k, self.kind, self.N, self.omega_dtype = rhqr_sketch_shape(self.handle)
+
+    def close(self):
+        if self.handle:
+            rhqr_sketch_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def export(self, device="cuda"):
+        if self.kind == SRHT:
+            signs = torch.empty(self.N, dtype=torch.int8, device=device)
+            rows = torch.empty(self.k, dtype=torch.int32, device=device)
+            rhqr_sketch_export(self.handle, signs, rows, None, 0)
+            return {"signs": signs, "rows": rows}
+        G = torch.empty((self.k, self.n), dtype=TORCH_DTYPE[self.omega_dtype], device=device)
+        rhqr_sketch_export(self.handle, None, None, G, self.n)
+        return {"G": G}
+
+    def apply(self, X: torch.Tensor, m: int) -> torch.Tensor:
+        """Z = Psi_m X (Algorithm 1), X column-major n x c."""
+        n, c = X.shape
+        ws_b = rhqr_sketch_apply_workspace(self.handle, m, dtype_code(X), n, c)
+        ws = torch.empty(max(ws_b, 1), dtype=torch.uint8, device=X.device)
+        Z = colmajor(torch.zeros((self.k + m, c), dtype=torch.float64, device=X.device))
+        rhqr_sketch_apply(self.handle, m, X, dtype_code(X), n, c, ld_of(X), Z, ld_of(Z), ws, ws_b)
+        return Z
+
+
+def make_opts(alg=ALG_REC, passes=1, limbs_first=2, limbs_refine=2, want_U=False, want_Q=True, scaling=0,
+              wait_budget=0):
+    o = rhqr_default_opts()
+    o.alg, o.passes, o.limbs_first, o.limbs_refine = alg, passes, limbs_first, limbs_refine
+    o.want_U, o.want_Q, o.scaling, o.wait_budget = int(want_U), int(want_Q), scaling, wait_budget
+    return o
+
+
+class Workspace:
+    """A reusable device workspace for rhqr_factor."""
+
+    def __init__(self, nbytes: int, device="cuda"):
+        self.nbytes = nbytes
+        self.buf = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
+
+
+def factor_outputs(sk: Sketch, n: int, m: int, dtype: torch.dtype, want_U: bool, want_Q: bool, device="cuda"):
+    p = sk.k + m
+    return {
+        "U": colmajor(torch.zeros((n, m), dtype=dtype, device=device)) if want_U else None,
+        "S": colmajor(torch.zeros((p, m), dtype=torch.float64, device=device)),
+        "T": colmajor(torch.zeros((m, m), dtype=torch.float64, device=device)),
+        "R": colmajor(torch.zeros((m, m), dtype=torch.float64, device=device)),
+        "Q": colmajor(torch.zeros((n, m), dtype=dtype, device=device)) if want_Q else None,
+        "info": torch.zeros(4, dtype=torch.int32, device=device),
+    }
+
+
+def factor(sk: Sketch, W: torch.Tensor, opts=None, out=None, ws: Workspace | None = None, stream=None, **kw):
+    """rhqr_factor on a column-major W; returns the dict of output tensors."""
+    n, m = W.shape
+    opts = opts or make_opts(**kw)
+    wt = dtype_code(W)
+    want_U = bool(opts.want_U) or opts.alg == ALG_LEFT
+    if out is None:
+        out = factor_outputs(sk, n, m, W.dtype, want_U, bool(opts.want_Q), W.device)
+    need = rhqr_workspace_size(sk.handle, n, m, wt, opts)
+    if ws is None or ws.nbytes < need:
+        ws = Workspace(need, W.device)
+    U, Q = out["U"], out["Q"]
+    rhqr_factor(sk.handle, W, wt, n, m, ld_of(W), opts, U, ld_of(U) if U is not None else n, out["S"],
+                ld_of(out["S"]), out["T"], out["R"], Q, ld_of(Q) if Q is not None else n, ws.buf, ws.nbytes,
+                out["info"], stream)
+    out["ws"] = ws
+    return out
+
+
+def reconstruct(sk: Sketch, S, T, R, Z, W, want_Q=True):
+    n, m = W.shape
+    U = colmajor(torch.zeros((n, m), dtype=W.dtype, device=W.device))
+    Q = colmajor(torch.zeros((n, m), dtype=W.dtype, device=W.device)) if want_Q else None
+    need = rhqr_workspace_size(sk.handle, n, m, dtype_code(W), None)
+    ws = torch.empty(need, dtype=torch.uint8, device=W.device)
+    rhqr_reconstruct(sk.handle, S, ld_of(S), T, R, Z, ld_of(Z), W, dtype_code(W), n, m, ld_of(W), U, ld_of(U), Q,
+                     ld_of(Q) if Q is not None else n, ws, need)
+    return U, Q
+
+
+def info(out) -> dict:
+    return read_info(out["info"])
