@@ -184,6 +184,22 @@ rhqr_status rhqr_reconstruct(rhqr_sketch s, const double *S, int64_t lds, const 
                              void *Q, int64_t ldq, void *ws, size_t ws_bytes,
                              rhqr_stream_t stream);
 
+/*
+ * Instrumentation (no counterpart in the paper).
+ * rhqr_launch_count: number of kernels this library has launched so far in the
+ *   process (every launch site counts itself; host-side counter).
+ * rhqr_profile_enable(1): reset the phase timers and start recording a pair of
+ *   CUDA events around each phase on the stream the phase is launched on;
+ *   (0) stops recording.  rhqr_profile_read copies, for phase i < n, the summed
+ *   event time in milliseconds and the number of timed calls, synchronising on
+ *   the recorded events; returns the number of phases.  Phases: 0 sketch
+ *   (Algorithm 1), 1 Householder QR of the sketch, 2 T factor, 3 row solves /
+ *   Q formation, 4 other small FP64 work, 5 left-looking column steps.
+ */
+int64_t rhqr_launch_count(void);
+void rhqr_profile_enable(int32_t on);
+int32_t rhqr_profile_read(double *ms /* host, n */, int64_t *calls /* host, n */, int32_t n);
+
 #ifdef __cplusplus
 }
 #endif

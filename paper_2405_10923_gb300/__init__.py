@@ -89,7 +89,12 @@ _SIGNATURES = {
                            _p, _i64, _p, _sz, _p, _p]),
     "rhqr_reconstruct": (_i32, [_p, _p, _i64, _p, _p, _p, _i64, _p, _i32, _i64, _i32, _i64, _p, _i64, _p, _i64, _p,
                                 _sz, _p]),
+    "rhqr_launch_count": (_i64, []),
+    "rhqr_profile_enable": (None, [_i32]),
+    "rhqr_profile_read": (_i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
 }
+
+PHASES = ["sketch", "hqr", "tfactor", "solve", "small", "left_step"]
 
 
 def header_functions() -> list[str]:
@@ -241,6 +246,23 @@ def rhqr_reconstruct(s, S, lds, T, R, Z, ldz, W, wt, n, m, ldw, U, ldu, Q, ldq, 
     _check("rhqr_reconstruct", load().rhqr_reconstruct(s, _ptr(S), lds, _ptr(T), _ptr(R), _ptr(Z), ldz, _ptr(W), wt, n,
                                                        m, ldw, _ptr(U), ldu, _ptr(Q), ldq, _ptr(ws), ws_bytes,
                                                        _stream(stream)))
+
+
+def rhqr_launch_count() -> int:
+    return load().rhqr_launch_count()
+
+
+def rhqr_profile_enable(on: bool) -> None:
+    load().rhqr_profile_enable(1 if on else 0)
+
+
+def rhqr_profile_read() -> dict:
+    """{phase: (milliseconds, calls)} for the phases recorded since enabling."""
+    n = len(PHASES)
+    ms = (ctypes.c_double * n)()
+    calls = (_i64 * n)()
+    load().rhqr_profile_read(ms, calls, n)
+    return {PHASES[i]: (ms[i], int(calls[i])) for i in range(n)}
 
 
 def read_info(info_tensor) -> dict:

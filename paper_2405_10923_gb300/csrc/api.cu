@@ -231,6 +231,8 @@ rhqr_status rhqr_sketch_apply_workspace(rhqr_sketch s, int32_t m, int32_t xt, in
                                         size_t *bytes) {
   if (s == nullptr || bytes == nullptr || !valid_dtype_hd(xt) || c < 1 || m < 0 || n <= m) return RHQR_EINVAL;
   *bytes = sketch_apply_workspace_bytes(s->view, m, xt, n, c);
+  if (xt == RHQR_F32 && sketch_tc_supported(s->view, n, m, c))
+    *bytes = std::max(*bytes, sketch_tc_workspace_bytes(s->view, n, m, c));
   return RHQR_OK;
 }
 
@@ -247,6 +249,9 @@ rhqr_status rhqr_sketch_apply(rhqr_sketch s, int32_t m, const void *X, int32_t x
   if (s == nullptr || X == nullptr || Z == nullptr || !valid_dtype_hd(xt) || c < 1) return RHQR_EINVAL;
   RHQR_TRY(check_sketch_shape(s->view, n, m));
   if (ldx < n || ldz < (int64_t)s->view.k + m) return RHQR_EINVAL;
+  // float32 data with a 16-bit Gaussian operator: tensor cores, exact 3-limb split
+  if (xt == RHQR_F32 && sketch_tc_supported(s->view, n, m, c) && ldx % 4 == 0 && ((uintptr_t)X % 16) == 0)
+    return sketch_apply_tc(s->view, m, (const float *)X, n, c, ldx, 3, Z, ldz, ws, ws_bytes, (cudaStream_t)stream);
   return sketch_apply_simt(s->view, m, X, xt, n, c, ldx, Z, ldz, ws, ws_bytes, (cudaStream_t)stream);
 }
 
@@ -269,7 +274,7 @@ static size_t sketch_ws_for_factor(const SketchView &v, int64_t n, int32_t m, in
   size_t b = sketch_apply_workspace_bytes(v, m, wt, n, m);
   if (v.kind == RHQR_SKETCH_GAUSSIAN && (v.omega_dtype == RHQR_BF16 || v.omega_dtype == RHQR_F16) &&
       wt == RHQR_F32)
-    b = std::max(b, sketch_tc_workspace_bytes(v, n, m));
+    b = std::max(b, sketch_tc_workspace_bytes(v, n, m, m));
   (void)o;
   return b;
 }
@@ -299,8 +304,8 @@ static rhqr_status carve_rec(Carver &c, const SketchView &v, int64_t n, int32_t 
 static rhqr_status sketch_for_pass(const SketchView &v, int32_t m, const void *X, int32_t wt, int64_t n,
                                    int64_t ldx, double *Z, int64_t ldz, int limbs, RecBuffers &b, cudaStream_t st) {
   if (v.kind == RHQR_SKETCH_GAUSSIAN && (v.omega_dtype == RHQR_BF16 || v.omega_dtype == RHQR_F16) &&
-      wt == RHQR_F32 && sketch_tc_supported(v, n, m)) {
-    return sketch_apply_tc(v, m, (const float *)X, n, ldx, limbs, Z, ldz, b.sk_ws, b.sk_bytes, st);
+      wt == RHQR_F32 && sketch_tc_supported(v, n, m, m)) {
+    return sketch_apply_tc(v, m, (const float *)X, n, m, ldx, limbs, Z, ldz, b.sk_ws, b.sk_bytes, st);
   }
   return sketch_apply_simt(v, m, X, wt, n, m, ldx, Z, ldz, b.sk_ws, b.sk_bytes, st);
 }
@@ -316,11 +321,17 @@ static rhqr_status rec_typed(const SketchView &v, const T *W, int32_t wt, int64_
   for (int pass = 0; pass < o.passes; ++pass) {
     const bool last = (pass == o.passes - 1);
     int limbs = pass == 0 ? o.limbs_first : o.limbs_refine;
-    RHQR_TRY(sketch_for_pass(v, m, X, wt, n, ldx, b.Z, p, limbs, b, st));
+    {
+      PhaseScope ps(PH_SKETCH, st);
+      RHQR_TRY(sketch_for_pass(v, m, X, wt, n, ldx, b.Z, p, limbs, b, st));
+    }
     double *Sdst = last ? S : b.Spass;
     int64_t ldsd = last ? lds : p;
-    RHQR_TRY(householder_qr_small(b.Z, p, p, m, Sdst, ldsd, b.Rpass, b.beta, o.scaling, b.hqr_ws, b.hqr_bytes, info,
-                                  budget, st));
+    {
+      PhaseScope ps(PH_HQR, st);
+      RHQR_TRY(householder_qr_small(b.Z, p, p, m, Sdst, ldsd, b.Rpass, b.beta, o.scaling, b.hqr_ws, b.hqr_bytes,
+                                    info, budget, st));
+    }
     if (pass == 0) {
       RHQR_TRY(copy_f64(b.Rpass, (int64_t)m * m, b.Racc, st));
     } else {
@@ -328,7 +339,11 @@ static rhqr_status rec_typed(const SketchView &v, const T *W, int32_t wt, int64_
       RHQR_TRY(copy_f64(b.Rtmp, (int64_t)m * m, b.Racc, st));
     }
     if (last) {
-      RHQR_TRY(t_factor_small(S, lds, p, m, b.beta, b.SS, Tm, st));
+      {
+        PhaseScope ps(PH_TFACTOR, st);
+        RHQR_TRY(t_factor_small(S, lds, p, m, b.beta, b.SS, Tm, st));
+      }
+      PhaseScope ps(PH_SOLVE, st);
       if (o.want_U) {
         // Algorithm 6: U_1 = S_{1:m}, U_2 solves X_2 = U_2 ut(T^t S^t Z); Q = [I;0] - U T U_1^t
         RHQR_TRY(m_factor(Tm, S, lds, b.Z, p, p, m, b.StZ, b.M, st));
@@ -344,6 +359,7 @@ static rhqr_status rec_typed(const SketchView &v, const T *W, int32_t wt, int64_
       }
     } else {
       // Q_i = X_{i-1} R_i^{-1} becomes the next pass's input (in place in Q)
+      PhaseScope ps(PH_SOLVE, st);
       RHQR_TRY(pad_transpose<T>(b.Rpass, m, 1, (T *)b.TriT, st));
       RHQR_TRY(rows_solve<T>(X, ldx, 0, n, m, (const T *)b.TriT, Q, ldq, st));
       X = Q;

@@ -26,7 +26,24 @@ namespace rhqr {
     if (s_ != RHQR_OK) return s_;      \
   } while (0)
 
-#define RHQR_LAUNCH_CHECK() RHQR_CUDA_TRY(cudaGetLastError())
+// Launch counter (read through rhqr_launch_count): every kernel launch of the
+// library is followed by RHQR_LAUNCH_CHECK, which counts it.
+void count_launch();
+#define RHQR_LAUNCH_CHECK()            \
+  do {                                 \
+    ::rhqr::count_launch();            \
+    RHQR_CUDA_TRY(cudaGetLastError()); \
+  } while (0)
+
+// Phase timing with CUDA events on the launching stream (rhqr_profile_*).
+enum Phase { PH_SKETCH = 0, PH_HQR, PH_TFACTOR, PH_SOLVE, PH_SMALL, PH_LEFT_STEP, PH_COUNT };
+struct PhaseScope {
+  int phase;
+  cudaStream_t st;
+  void *ev;
+  PhaseScope(int ph, cudaStream_t s);
+  ~PhaseScope();
+};
 
 inline size_t dtype_size(int32_t t) {
   switch (t) {

@@ -231,12 +231,20 @@ static rhqr_status apply_typed(const SketchView &s, int32_t m, const TX *X, int6
                                                                  chunk_len, part);
       break;
     case RHQR_BF16:
-      gauss_gemm_kernel<__nv_bfloat16, TX, float><<<grid, 256, 0, st>>>((const __nv_bfloat16 *)s.G, s.ldg, X, ldx, n,
-                                                                       m, s.k, c, chunk_len, part);
+      if (wide)
+        gauss_gemm_kernel<__nv_bfloat16, TX, double><<<grid, 256, 0, st>>>((const __nv_bfloat16 *)s.G, s.ldg, X, ldx,
+                                                                          n, m, s.k, c, chunk_len, part);
+      else
+        gauss_gemm_kernel<__nv_bfloat16, TX, float><<<grid, 256, 0, st>>>((const __nv_bfloat16 *)s.G, s.ldg, X, ldx,
+                                                                         n, m, s.k, c, chunk_len, part);
       break;
     case RHQR_F16:
-      gauss_gemm_kernel<__half, TX, float><<<grid, 256, 0, st>>>((const __half *)s.G, s.ldg, X, ldx, n, m, s.k, c,
-                                                                chunk_len, part);
+      if (wide)
+        gauss_gemm_kernel<__half, TX, double><<<grid, 256, 0, st>>>((const __half *)s.G, s.ldg, X, ldx, n, m, s.k, c,
+                                                                   chunk_len, part);
+      else
+        gauss_gemm_kernel<__half, TX, float><<<grid, 256, 0, st>>>((const __half *)s.G, s.ldg, X, ldx, n, m, s.k, c,
+                                                                  chunk_len, part);
       break;
     default:
       return RHQR_EINVAL;

@@ -1,10 +1,547 @@
+// Gaussian sketch Omega X on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// Z_Omega = G X_2 / sqrt(k) (Section 2.3) with G (k x n) stored in bf16 or f16
+// and X (n x c) in float32.  X is split into L 16-bit limbs,
+// X = X_1 + ... + X_L (X_1 = round(X), X_2 = round(X - X_1), ...), so that the
+// products of the stored G with every limb are exact.
+//
+// Tensor-core accumulation adds each 16-deep product block to the float32
+// accumulator with truncation, so its error grows with the number of MMAs
+// that hit one accumulator.  The accumulator is therefore drained every
+// `kdrain` rows of X into a float32 running sum kept in the other half of
+// tensor memory and updated with round-to-nearest adds; the per-chunk results
+// are summed in float64 in a fixed order.
+//
+// One CTA owns a 256 x Nt output tile (two M = 128 accumulators, Nt <= 128
+// columns) and one K-chunk of X rows.
+//   warp 0       : TMA producer: G tile (256 x 64 bf16, 128-byte swizzle) and
+//                  X tile (64 rows x Nt float32) per stage
+//   warp 1       : tensor-memory allocation and the single MMA-issuing thread
+//   warps 4..7   : converters: staged X -> L limbs in the K-major 128-byte
+//                  swizzled layout the MMA reads (rows < m are zeroed)
+//   warps 8..15  : drainers: fresh accumulator + running sum -> running sum;
+//                  at the end the running sums go to a float32 partial
+//                  [chunk][column][row] in global memory
+// Every wait on an mbarrier is bounded; a wait that runs out sets an error
+// flag, the other roles stop, TMA copies still in flight are awaited (bounded)
+// and tensor memory is released before the block exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "sketch_tc.cuh"
 
 namespace rhqr {
-bool sketch_tc_supported(const SketchView &, int64_t, int32_t) { return false; }
-size_t sketch_tc_workspace_bytes(const SketchView &, int64_t, int32_t) { return 0; }
-rhqr_status sketch_apply_tc(const SketchView &, int32_t, const float *, int64_t, int64_t, int, double *, int64_t,
-                            void *, size_t, cudaStream_t) {
-  return RHQR_ENOTSUP;
+namespace tc {
+
+constexpr int BM = 256;  // rows of G per CTA
+constexpr int BK = 64;   // rows of X per stage (128 bytes of a 16-bit limb)
+constexpr int NT = 128;  // max columns of X per CTA
+constexpr int MAXC = 256;
+constexpr int NUM_THREADS = 512;
+constexpr int CONV_WARP0 = 4, NUM_CONV_WARPS = 4;
+constexpr int DRAIN_WARP0 = 8, NUM_DRAIN_WARPS = 8;
+constexpr int A_BYTES = BM * BK * 2;    // 32 KiB
+constexpr int B_BYTES = NT * BK * 2;    // 16 KiB per limb
+constexpr int X_BYTES = NT * BK * 4;    // 32 KiB staging
+constexpr int KDRAIN = 256;             // rows of X between drains
+constexpr int RUN_COL = 256;            // tensor-memory column of the running sums
+
+struct Params {
+  int64_t n;
+  int32_t m, m8, c, Nt, k;
+  int64_t kchunk;
+  int32_t limbs, stages, kdrain;
+  int32_t xbytes;  // bytes of one X box: 64 rows x Nt columns of float32
+  float *part;  // [nch][c][k]
+  int *err;
+  long long budget;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait.  Returns false if the block is aborting or the budget ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long budget, int *err,
+                                          volatile int *abort_s) {
+  long long it = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_s) return false;
+    if (++it > budget) {
+      atomicExch(err, 1);
+      *abort_s = 1;
+      return false;
+    }
+  }
+  return true;
+}
+// warp-uniform bounded wait (every lane polls, the decision is unanimous)
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, long long budget, int *err,
+                                          volatile int *abort_s) {
+  bool ok = mbar_wait(bar, parity, budget, err, abort_s);
+  return __all_sync(0xffffffffu, ok);
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (bf16 or f16 inputs, f32 accumulate)
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+#define RHQR_R32(r)                                                                                              \
+  "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),    \
+      "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),     \
+      "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),    \
+      "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+#define RHQR_W32(r)                                                                                               \
+  "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),   \
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), \
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), \
+      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+
+// 32 consecutive columns of this warp's 32 tensor-memory lanes (one per thread)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : RHQR_R32(r)
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      RHQR_W32(r)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes grouped in 8-row (1024-byte) atoms.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused with this swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: f32 accumulator, K-major A and B.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N, uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <class TL>
+struct Limb;
+template <>
+struct Limb<__nv_bfloat16> {
+  static constexpr uint32_t fmt = 1;
+  __device__ static __forceinline__ uint32_t pack(float a, float b, float &ra, float &rb) {
+    __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+    ra = a - __bfloat162float(ha);
+    rb = b - __bfloat162float(hb);
+    return (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+  }
+};
+template <>
+struct Limb<__half> {
+  static constexpr uint32_t fmt = 0;
+  __device__ static __forceinline__ uint32_t pack(float a, float b, float &ra, float &rb) {
+    __half ha = __float2half_rn(a), hb = __float2half_rn(b);
+    ra = a - __half2float(ha);
+    rb = b - __half2float(hb);
+    return (uint32_t)__half_as_ushort(ha) | ((uint32_t)__half_as_ushort(hb) << 16);
+  }
+};
+
+template <class TL>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    sketch_tc_kernel(const __grid_constant__ CUtensorMap tmapG, const __grid_constant__ CUtensorMap tmapX, Params P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int S = P.stages, L = P.limbs;
+  const int stage_bytes = A_BYTES + X_BYTES + L * B_BYTES;  // A | X staging | limbs
+  uint64_t *bars = (uint64_t *)(smem + S * stage_bytes);
+  uint64_t *full_a = bars, *full_b = bars + 4, *empty = bars + 8, *xempty = bars + 12;
+  uint64_t *fresh_full = bars + 16, *fresh_empty = bars + 17;
+  uint32_t *tmem_slot = (uint32_t *)(bars + 18);
+  volatile int *abort_s = (volatile int *)(bars + 19);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mt = blockIdx.x, nt = blockIdx.y, ch = blockIdx.z;
+  const int col0 = nt * P.Nt;
+  const int64_t x_begin = (int64_t)P.m8 + (int64_t)ch * P.kchunk;
+  const int64_t x_end = min(P.n, x_begin + P.kchunk);
+  const int steps = (int)((x_end - x_begin + BK - 1) / BK);
+  const int per_drain = P.kdrain / BK;
+  const int drains = (steps + per_drain - 1) / per_drain;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 4; ++s) {
+      mbar_init(full_a + s, 1);
+      mbar_init(full_b + s, NUM_CONV_WARPS);
+      mbar_init(empty + s, 1);
+      mbar_init(xempty + s, NUM_CONV_WARPS);
+    }
+    mbar_init(fresh_full, 1);
+    mbar_init(fresh_empty, NUM_DRAIN_WARPS);
+    *abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      bool aborted = false;
+      for (int i = 0; i < steps; ++i) {
+        const int s = i % S;
+        const uint32_t ph = (uint32_t)(i / S) & 1u;
+        if (!mbar_wait(empty + s, ph ^ 1u, P.budget, P.err, abort_s) ||
+            !mbar_wait(xempty + s, ph ^ 1u, P.budget, P.err, abort_s)) {
+          aborted = true;
+          break;
+        }
+        uint8_t *st = smem + s * stage_bytes;
+        mbar_expect_tx(full_a + s, (uint32_t)(A_BYTES + P.xbytes));
+        const int xr = (int)(x_begin + (int64_t)i * BK);
+        tma_load_2d(st, &tmapG, full_a + s, xr, mt * BM);
+        tma_load_2d(st + A_BYTES, &tmapX, full_a + s, xr, col0);
+        ++issued;
+      }
+      if (aborted) {  // wait (bounded) for the copies still in flight
+        for (int i = max(0, issued - S); i < issued; ++i) {
+          long long it = 0;
+          while (!mbar_try_wait(full_a + (i % S), (uint32_t)(i / S) & 1u) && ++it < P.budget) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(128, P.Nt, Limb<TL>::fmt);
+      int i = 0;
+      for (int d = 0; d < drains && i < steps; ++d) {
+        if (d > 0 && !mbar_wait(fresh_empty, (uint32_t)(d - 1) & 1u, P.budget, P.err, abort_s)) break;
+        tc_fence_after();
+        bool ok = true;
+        for (int j = 0; j < per_drain && i < steps; ++j, ++i) {
+          const int s = i % S;
+          const uint32_t ph = (uint32_t)(i / S) & 1u;
+          if (!mbar_wait(full_a + s, ph, P.budget, P.err, abort_s) ||
+              !mbar_wait(full_b + s, ph, P.budget, P.err, abort_s)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_base = smem_u32(smem + s * stage_bytes);
+          const uint32_t b_base = a_base + A_BYTES + X_BYTES;
+          for (int h = 0; h < 2; ++h)
+            for (int kk = 0; kk < BK / 16; ++kk)
+              for (int l = 0; l < L; ++l) {
+                uint64_t ad = sw128_desc(a_base + h * (128 * 128) + kk * 32);
+                uint64_t bd = sw128_desc(b_base + l * B_BYTES + kk * 32);
+                mma_f16(tmem + (uint32_t)(h * NT), ad, bd, idesc, (uint32_t)((j | kk | l) != 0));
+              }
+          mma_commit(empty + s);
+        }
+        mma_commit(fresh_full);
+        if (!ok) break;
+      }
+    }
+  } else if (warp >= CONV_WARP0 && warp < CONV_WARP0 + NUM_CONV_WARPS) {
+    // converters: 128 threads, X staging (col-major 64 rows x Nt) -> limbs
+    const int ct = threadIdx.x - CONV_WARP0 * 32;
+    for (int i = 0; i < steps; ++i) {
+      const int s = i % S;
+      const uint32_t ph = (uint32_t)(i / S) & 1u;
+      if (!warp_wait(full_a + s, ph, P.budget, P.err, abort_s)) break;
+      uint8_t *st = smem + s * stage_bytes;
+      const float *xs = reinterpret_cast<const float *>(st + A_BYTES);
+      uint8_t *bst = st + A_BYTES + X_BYTES;
+      const int64_t r0 = x_begin + (int64_t)i * BK;
+      const bool top = r0 < P.m;  // rows below m are the exact top block: excluded
+      for (int q = ct; q < P.Nt * 8; q += NUM_CONV_WARPS * 32) {
+        const int nn = q >> 3, cidx = q & 7;
+        const float4 *src = reinterpret_cast<const float4 *>(xs + nn * BK + cidx * 8);
+        float4 a = src[0], b = src[1];
+        float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        if (top) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            if (r0 + cidx * 8 + e < P.m) v[e] = 0.f;
+        }
+        const uint32_t off = (uint32_t)nn * 128u + ((uint32_t)(cidx ^ (nn & 7)) << 4);
+        for (int l = 0; l < L; ++l) {
+          uint4 w;
+          float r[8];
+          w.x = Limb<TL>::pack(v[0], v[1], r[0], r[1]);
+          w.y = Limb<TL>::pack(v[2], v[3], r[2], r[3]);
+          w.z = Limb<TL>::pack(v[4], v[5], r[4], r[5]);
+          w.w = Limb<TL>::pack(v[6], v[7], r[6], r[7]);
+          *reinterpret_cast<uint4 *>(bst + l * B_BYTES + off) = w;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] = r[e];
+        }
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(full_b + s);
+        mbar_arrive(xempty + s);
+      }
+    }
+  } else if (warp >= DRAIN_WARP0) {
+    // drainers: warp -> (half h, lane quarter qd); thread -> one accumulator row
+    const int dw = warp - DRAIN_WARP0;
+    const int h = dw >> 2, qd = warp & 3;
+    const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
+    const uint32_t fresh = tmem + lane_base + (uint32_t)(h * NT);
+    const uint32_t run = tmem + lane_base + (uint32_t)(RUN_COL + h * NT);
+    const int row = mt * BM + h * 128 + qd * 32 + lane;
+    bool ok = true;
+    for (int d = 0; d < drains; ++d) {
+      if (!warp_wait(fresh_full, (uint32_t)d & 1u, P.budget, P.err, abort_s)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const bool last = (d == drains - 1);
+      for (int c0 = 0; c0 < P.Nt; c0 += 32) {
+        uint32_t f[32], r[32];
+        tmem_ld32(fresh + c0, f);
+        if (d > 0) tmem_ld32(run + c0, r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          float v = __uint_as_float(f[j]);
+          if (d > 0) v = __fadd_rn(__uint_as_float(r[j]), v);
+          r[j] = __float_as_uint(v);
+        }
+        if (last) {
+          if (row < P.k) {
+            for (int j = 0; j < 32; ++j) {
+              const int cc = col0 + c0 + j;
+              if (cc < P.c && c0 + j < P.Nt)
+                P.part[((int64_t)ch * P.c + cc) * P.k + row] = __uint_as_float(r[j]);
+            }
+          }
+        } else {
+          tmem_st32(run + c0, r);
+        }
+      }
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(fresh_empty);
+    }
+    (void)ok;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// Z[ztop + r, c] = scale * sum_chunk part[chunk][c][r]  (float64, fixed order)
+__global__ void reduce_part_kernel(const float *part, int32_t nch, int32_t k, int32_t c, int32_t ztop, double scale,
+                                   double *Z, int64_t ldz) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)k * c) return;
+  double acc = 0.0;
+  for (int ch = 0; ch < nch; ++ch) acc += (double)part[(int64_t)ch * k * c + idx];
+  int64_t col = idx / k, r = idx - col * k;
+  Z[col * ldz + ztop + r] = acc * scale;
+}
+
+__global__ void copy_top_f32_kernel(const float *X, int64_t ldx, int32_t m, int32_t c, double *Z, int64_t ldz) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)m * c) return;
+  int64_t col = idx / m, i = idx - col * m;
+  Z[col * ldz + i] = (double)X[col * ldx + i];
+}
+
+}  // namespace tc
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (fn == nullptr) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      (void)cudaGetLastError();
+  }
+  return fn;
+}
+
+// Work split: the CTAs of one launch cover (k/256) x (c/Nt) tiles times nch
+// K-chunks; nch is chosen so the grid fills the 152 SMs in whole waves.
+static int64_t tc_nchunks(const SketchView &s, int64_t n, int32_t m, int32_t c, int64_t *kchunk) {
+  int64_t K = n - (m & ~7);
+  int64_t Np = ceil_div(c, 16) * 16;
+  int64_t tiles = ceil_div(s.k, tc::BM) * ceil_div(Np, tc::NT);
+  int64_t want = std::max<int64_t>(1, 152 / std::max<int64_t>(1, tiles));
+  if (tiles * want < 152) want = ceil_div(152 * ceil_div(tiles, 152), tiles);
+  int64_t kc = ceil_div(ceil_div(K, want), tc::KDRAIN) * tc::KDRAIN;
+  kc = std::max<int64_t>(kc, tc::KDRAIN);
+  if (kchunk) *kchunk = kc;
+  return ceil_div(K, kc);
+}
+
+bool sketch_tc_supported(const SketchView &s, int64_t n, int32_t m, int32_t c) {
+  if (s.kind != RHQR_SKETCH_GAUSSIAN) return false;
+  if (s.omega_dtype != RHQR_BF16 && s.omega_dtype != RHQR_F16) return false;
+  if (c < 1 || c > tc::MAXC || m < 0 || n <= m || n > (int64_t(1) << 31) - 1) return false;
+  if ((s.ldg * 2) % 16 != 0) return false;
+  return tensor_map_encoder() != nullptr;
+}
+
+size_t sketch_tc_workspace_bytes(const SketchView &s, int64_t n, int32_t m, int32_t c) {
+  if (c < 1 || n <= m) return 0;
+  return align_up((size_t)tc_nchunks(s, n, m, c, nullptr) * s.k * c * sizeof(float), 256) + 256;
+}
+
+rhqr_status sketch_apply_tc(const SketchView &s, int32_t m, const float *X, int64_t n, int32_t c, int64_t ldx,
+                            int limbs, double *Z, int64_t ldz, void *ws, size_t ws_bytes, cudaStream_t st) {
+  if (!sketch_tc_supported(s, n, m, c)) return RHQR_ENOTSUP;
+  if (limbs < 1 || limbs > 3) return RHQR_EINVAL;
+  if ((ldx % 4) != 0 || ((uintptr_t)X % 16) != 0) return RHQR_ENOTSUP;
+  int64_t kchunk = 0;
+  const int64_t nch = tc_nchunks(s, n, m, c, &kchunk);
+  size_t part_bytes = align_up((size_t)nch * s.k * c * sizeof(float), 256);
+  if (ws_bytes < part_bytes + 256) return RHQR_ENOMEM;
+  float *part = (float *)ws;
+  int *err = (int *)((char *)ws + part_bytes);
+  RHQR_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+
+  const int32_t Np = (int32_t)ceil_div(c, 16) * 16;
+  const int32_t Nt = std::min<int32_t>(tc::NT, Np);
+  CUtensorMap mapG, mapX;
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)s.k};
+    cuuint64_t strides[1] = {(cuuint64_t)s.ldg * 2};
+    cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult cr = tensor_map_encoder()(&mapG,
+                                       s.omega_dtype == RHQR_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                  : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                                       2, const_cast<void *>(s.G), dims, strides, box, estr,
+                                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return RHQR_ECUDA;
+  }
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)c};
+    cuuint64_t strides[1] = {(cuuint64_t)ldx * 4};
+    cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)Nt};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult cr = tensor_map_encoder()(&mapX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), dims,
+                                       strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return RHQR_ECUDA;
+  }
+
+  tc::Params P;
+  P.n = n;
+  P.m = m;
+  P.m8 = m & ~7;
+  P.c = c;
+  P.Nt = Nt;
+  P.k = s.k;
+  P.kchunk = kchunk;
+  P.limbs = limbs;
+  P.stages = 2;
+  P.kdrain = tc::KDRAIN;
+  P.xbytes = tc::BK * Nt * 4;
+  P.part = part;
+  P.err = err;
+  P.budget = 4000000LL;
+  size_t smem = 1024 + (size_t)P.stages * (tc::A_BYTES + tc::X_BYTES + (size_t)limbs * tc::B_BYTES) + 256;
+  dim3 grid((unsigned)ceil_div(s.k, tc::BM), (unsigned)ceil_div(Np, Nt), (unsigned)nch);
+  if (s.omega_dtype == RHQR_BF16) {
+    RHQR_CUDA_TRY(cudaFuncSetAttribute(tc::sketch_tc_kernel<__nv_bfloat16>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    tc::sketch_tc_kernel<__nv_bfloat16><<<grid, tc::NUM_THREADS, smem, st>>>(mapG, mapX, P);
+  } else {
+    RHQR_CUDA_TRY(
+        cudaFuncSetAttribute(tc::sketch_tc_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    tc::sketch_tc_kernel<__half><<<grid, tc::NUM_THREADS, smem, st>>>(mapG, mapX, P);
+  }
+  RHQR_LAUNCH_CHECK();
+  if (m > 0) {
+    tc::copy_top_f32_kernel<<<(unsigned)ceil_div((int64_t)m * c, 256), 256, 0, st>>>(X, ldx, m, c, Z, ldz);
+    RHQR_LAUNCH_CHECK();
+  }
+  int64_t tot = (int64_t)s.k * c;
+  tc::reduce_part_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(part, (int32_t)nch, s.k, c, m,
+                                                                       1.0 / sqrt((double)s.k), Z, ldz);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
+}
+
 }  // namespace rhqr

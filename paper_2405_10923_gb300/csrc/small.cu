@@ -245,6 +245,7 @@ rhqr_status householder_qr_small(const double *Z, int64_t ldz, int64_t p, int32_
   int grid = hqr_grid(p);
   void *kargs[] = {&args};
   RHQR_CUDA_TRY(cudaLaunchCooperativeKernel((void *)hqr_coop_kernel, dim3(grid), dim3(256), kargs, 0, st));
+  count_launch();
   return RHQR_OK;
 }
 

@@ -64,3 +64,51 @@ def to_dtype(W: np.ndarray, dtype: str) -> np.ndarray:
     if dtype == "f32":
         return np.asfortranarray(W, dtype=np.float32)
     raise ValueError(dtype)
+
+
+# ---------------------------------------------------------------------------
+# GPU-resident variants (same recipes; torch's CUDA generator) for full sizes
+# ---------------------------------------------------------------------------
+
+
+def _device_orthonormal(G):
+    """Orthonormal columns spanning G (n x m, float64 on the device) by two
+    Cholesky-QR passes: the m x m Gram matrices are factored on the host."""
+    import torch
+
+    A = G
+    for _ in range(2):
+        C = (A.t() @ A).cpu().numpy()
+        Rinv = np.linalg.inv(np.linalg.cholesky(C).T)
+        A = A @ torch.tensor(Rinv, dtype=torch.float64, device=A.device)
+    return A
+
+
+def device_spectrum(n: int, m: int, cond: float, seed: int, dtype=None, device="cuda"):
+    """W = A diag(sigma) B built in float64 on the device, returned column-major
+    in `dtype` (torch dtype, default float32).  A: orthonormal basis of an n x m
+    Gaussian matrix; B: Q factor of an m x m Gaussian matrix (host QR)."""
+    import torch
+
+    dtype = dtype or torch.float32
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    A = _device_orthonormal(torch.randn((n, m), generator=g, dtype=torch.float64, device=device))
+    Bm = torch.tensor(orthonormal(m, m, np.random.default_rng(seed)), dtype=torch.float64, device=device)
+    sig = torch.tensor(log_spectrum(m, cond), dtype=torch.float64, device=device)
+    W = (A * sig[None, :]) @ Bm
+    del A
+    out = torch.empty((m, n), dtype=dtype, device=device).t()
+    out.copy_(W)
+    return out
+
+
+def device_gaussian(n: int, m: int, seed: int, dtype=None, device="cuda"):
+    import torch
+
+    dtype = dtype or torch.float32
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    out = torch.empty((m, n), dtype=dtype, device=device).t()
+    out.copy_(torch.randn((n, m), generator=g, dtype=torch.float64, device=device))
+    return out

@@ -1,0 +1,84 @@
+"""Tensor-core (tcgen05) Gaussian sketch and the mixed-precision recRHQR path,
+against the FP64 oracle using the same 16-bit Gaussian operator.
+
+Tolerances: the 3-limb split represents float32 data exactly, so the only
+error is the float32 accumulation inside a K-chunk of 8192 rows:
+|Z - Z_oracle| <= 2e-5 max|Z_oracle|.  The factorisation tolerances are the
+stated ones: <= 5e-3 before refinement (one bf16 limb, well-conditioned W) and
+<= 1e-5 after refinement for ||I - (Psi Q)^t Psi Q||_2 and ||W - QR||/||W||."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+import rhqr_inputs as ri  # noqa: E402
+from oracle import metrics, rhqr, sketch  # noqa: E402
+
+
+def _dev(W, dtype=torch.float32):
+    import paper_2405_10923_gb300 as rh
+
+    return rh.colmajor(torch.tensor(W, dtype=dtype, device="cuda"))
+
+
+def _np(t):
+    return t.detach().double().cpu().numpy()
+
+
+@pytest.mark.parametrize("dt", ["bf16", "f16"])
+@pytest.mark.parametrize("n,m,c,k", [(50000, 16, 16, 1024), (40003, 13, 40, 300), (70000, 256, 256, 512),
+                                     (9000, 0, 7, 256), (20000, 5, 256, 1024)])
+def test_tc_sketch_matches_oracle(gpu_lib, dt, n, m, c, k):
+    from paper_2405_10923_gb300 import torch_api as ta
+
+    code = gpu_lib.BF16 if dt == "bf16" else gpu_lib.F16
+    X = ri.gaussian(n, c, 70).astype(np.float32).astype(np.float64)
+    sk = ta.Sketch(n, k, gpu_lib.GAUSSIAN, 71, code)
+    Z = _np(sk.apply(_dev(X), m))
+    Zo = sketch.rh_sketch(X, m, sketch.GaussianSketch(n, k, 71, dt))
+    assert np.array_equal(Z[:m], Zo[:m])
+    assert np.max(np.abs(Z - Zo)) <= 2e-5 * np.abs(Zo).max()
+    sk.close()
+
+
+def _orth_exact(gpu_lib, sk, Q, m):
+    """||I - (Psi Q)^t Psi Q||_2 with Psi Q accumulated in float64 on the GPU
+    (the same stored operator, the SIMT float64 path)."""
+    Z = sk.apply(Q.double().contiguous().t().contiguous().t(), m)
+    G = (Z.t() @ Z).cpu().numpy()
+    return float(np.max(np.abs(np.linalg.eigvalsh(np.eye(G.shape[0]) - G))))
+
+
+def test_mixed_rec_one_pass_well_conditioned(gpu_lib):
+    from paper_2405_10923_gb300 import torch_api as ta
+
+    n, m, k = 1 << 17, 64, 256
+    W = ri.gaussian(n, m, 80).astype(np.float32).astype(np.float64)
+    sk = ta.Sketch(n, k, gpu_lib.GAUSSIAN, 81, gpu_lib.BF16)
+    out = ta.factor(sk, _dev(W), alg=gpu_lib.ALG_REC, passes=1, limbs_first=1)
+    torch.cuda.synchronize()
+    assert ta.info(out)["status"] == 0
+    osk = sketch.GaussianSketch(n, k, 81, "bf16")
+    Q = _np(out["Q"])
+    assert metrics.sketch_orthogonality(Q, osk) <= 5e-3
+    assert metrics.residual(W, Q, _np(out["R"])) <= 1e-5
+    sk.close()
+
+
+@pytest.mark.parametrize("cond", [1e4, 1e10])
+def test_mixed_rec_refined_meets_tolerance(gpu_lib, cond):
+    from paper_2405_10923_gb300 import torch_api as ta
+
+    n, m, k = 1 << 17, 64, 256
+    W = ri.spectrum(n, m, cond, 82).astype(np.float32).astype(np.float64)
+    sk = ta.Sketch(n, k, gpu_lib.GAUSSIAN, 83, gpu_lib.BF16)
+    out = ta.factor(sk, _dev(W), alg=gpu_lib.ALG_REC, passes=3, limbs_first=2, limbs_refine=2)
+    torch.cuda.synchronize()
+    assert ta.info(out)["status"] == 0 and ta.info(out)["passes_done"] == 3
+    osk = sketch.GaussianSketch(n, k, 83, "bf16")
+    Q = _np(out["Q"])
+    assert metrics.sketch_orthogonality(Q, osk) <= 1e-5
+    assert metrics.residual(W, Q, _np(out["R"])) <= 1e-5
+    sk.close()
