@@ -13,6 +13,7 @@
 #include "sketch.cuh"
 #include "sketch_tc.cuh"
 #include "small.cuh"
+#include "solve_tc.cuh"
 
 struct rhqr_sketch_s {
   rhqr::SketchView view;
@@ -264,6 +265,8 @@ rhqr_status rhqr_sketch_apply(rhqr_sketch s, int32_t m, const void *X, int32_t x
 struct RecBuffers {
   double *Z, *Spass, *Rpass, *Racc, *Rtmp, *beta, *SS, *StZ, *M, *Gm;
   char *TriT, *GT;
+  float *TriT64;  // padded to a multiple of the tensor-core panel width
+  int *err;
   char *hqr_ws;
   size_t hqr_bytes;
   char *sk_ws;
@@ -294,6 +297,11 @@ static rhqr_status carve_rec(Carver &c, const SketchView &v, int64_t n, int32_t 
   b.Gm = c.take<double>((size_t)m * m);
   b.TriT = c.take<char>(small_padded_bytes(m));
   b.GT = c.take<char>(small_padded_bytes(m));
+  {
+    int64_t mp64 = ceil_div(m, kSolvePanel) * kSolvePanel;
+    b.TriT64 = c.take<float>((size_t)mp64 * mp64);
+    b.err = c.take<int>(4);
+  }
   b.hqr_bytes = hqr_workspace_bytes(p, m);
   b.hqr_ws = c.take<char>(b.hqr_bytes);
   b.sk_bytes = sketch_ws_for_factor(v, n, m, wt, o);
@@ -308,6 +316,29 @@ static rhqr_status sketch_for_pass(const SketchView &v, int32_t m, const void *X
     return sketch_apply_tc(v, m, (const float *)X, n, m, ldx, limbs, Z, ldz, b.sk_ws, b.sk_bytes, st);
   }
   return sketch_apply_simt(v, m, X, wt, n, m, ldx, Z, ldz, b.sk_ws, b.sk_bytes, st);
+}
+
+// Q = X Tri^{-1} over all n rows: tensor cores for float32 data (m <= 256),
+// the SIMT substitution otherwise.
+template <class T>
+static rhqr_status solve_rows(const T *X, int64_t ldx, int64_t n, int32_t m, const double *Tri, T *Q, int64_t ldq,
+                              RecBuffers &b, cudaStream_t st);
+template <>
+rhqr_status solve_rows<float>(const float *X, int64_t ldx, int64_t n, int32_t m, const double *Tri, float *Q,
+                              int64_t ldq, RecBuffers &b, cudaStream_t st) {
+  if (solve_tc_supported(m)) {
+    int32_t mp64 = (int32_t)(ceil_div(m, kSolvePanel) * kSolvePanel);
+    RHQR_TRY(pad_transpose_to<float>(Tri, m, mp64, 1, b.TriT64, st));
+    return rows_solve_tc(X, ldx, 0, n, m, b.TriT64, mp64, Q, ldq, b.err, st);
+  }
+  RHQR_TRY(pad_transpose<float>(Tri, m, 1, (float *)b.TriT, st));
+  return rows_solve<float>(X, ldx, 0, n, m, (const float *)b.TriT, Q, ldq, st);
+}
+template <>
+rhqr_status solve_rows<double>(const double *X, int64_t ldx, int64_t n, int32_t m, const double *Tri, double *Q,
+                               int64_t ldq, RecBuffers &b, cudaStream_t st) {
+  RHQR_TRY(pad_transpose<double>(Tri, m, 1, (double *)b.TriT, st));
+  return rows_solve<double>(X, ldx, 0, n, m, (const double *)b.TriT, Q, ldq, st);
 }
 
 template <class T>
@@ -354,14 +385,12 @@ static rhqr_status rec_typed(const SketchView &v, const T *W, int32_t wt, int64_
         RHQR_TRY(top_from_s<T>(S, lds, m, U, ldu, st));
         if (Q != nullptr) RHQR_TRY(rows_form_q<T>(U, ldu, 0, m, m, (const T *)b.GT, Q, ldq, st));
       } else if (Q != nullptr) {
-        RHQR_TRY(pad_transpose<T>(b.Rpass, m, 1, (T *)b.TriT, st));
-        RHQR_TRY(rows_solve<T>(X, ldx, 0, n, m, (const T *)b.TriT, Q, ldq, st));
+        RHQR_TRY(solve_rows<T>(X, ldx, n, m, b.Rpass, Q, ldq, b, st));
       }
     } else {
       // Q_i = X_{i-1} R_i^{-1} becomes the next pass's input (in place in Q)
       PhaseScope ps(PH_SOLVE, st);
-      RHQR_TRY(pad_transpose<T>(b.Rpass, m, 1, (T *)b.TriT, st));
-      RHQR_TRY(rows_solve<T>(X, ldx, 0, n, m, (const T *)b.TriT, Q, ldq, st));
+      RHQR_TRY(solve_rows<T>(X, ldx, n, m, b.Rpass, Q, ldq, b, st));
       X = Q;
       ldx = ldq;
     }

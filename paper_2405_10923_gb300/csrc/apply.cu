@@ -152,14 +152,20 @@ static int rows_per_block(int32_t mp) {
 }
 
 template <class T>
-rhqr_status pad_transpose(const double *A, int32_t m, int upper, T *out, cudaStream_t st) {
-  int32_t mp = padded_m(m);
+rhqr_status pad_transpose_to(const double *A, int32_t m, int32_t mp, int upper, T *out, cudaStream_t st) {
+  if (mp < m) return RHQR_EINVAL;
   pad_transpose_kernel<T><<<(unsigned)ceil_div((int64_t)mp * mp, 256), 256, 0, st>>>(A, m, mp, upper, out);
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }
+template <class T>
+rhqr_status pad_transpose(const double *A, int32_t m, int upper, T *out, cudaStream_t st) {
+  return pad_transpose_to<T>(A, m, padded_m(m), upper, out, st);
+}
 template rhqr_status pad_transpose<float>(const double *, int32_t, int, float *, cudaStream_t);
 template rhqr_status pad_transpose<double>(const double *, int32_t, int, double *, cudaStream_t);
+template rhqr_status pad_transpose_to<float>(const double *, int32_t, int32_t, int, float *, cudaStream_t);
+template rhqr_status pad_transpose_to<double>(const double *, int32_t, int32_t, int, double *, cudaStream_t);
 
 template <class T, int MODE>
 static rhqr_status launch_rows(const T *X, int64_t ldx, int64_t row_begin, int64_t nrows, int32_t m, const T *TriT,

@@ -10,6 +10,8 @@ size_t small_padded_bytes(int32_t m);
 // out = A (m x m float64, ld m) transposed and padded to mp x mp, cast to T.
 template <class T>
 rhqr_status pad_transpose(const double *A, int32_t m, int upper, T *out, cudaStream_t st);
+template <class T>
+rhqr_status pad_transpose_to(const double *A, int32_t m, int32_t mp, int upper, T *out, cudaStream_t st);
 
 // Y[rows] = X[rows] Tri^{-1}  (TriT from pad_transpose with upper = 1)
 template <class T>

@@ -82,3 +82,43 @@ def test_mixed_rec_refined_meets_tolerance(gpu_lib, cond):
     assert metrics.sketch_orthogonality(Q, osk) <= 1e-5
     assert metrics.residual(W, Q, _np(out["R"])) <= 1e-5
     sk.close()
+
+
+# ---------------------------------------------------------------------------
+# tensor-core row solve Q = W R^{-1} (float32 data, m <= 256)
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("n,m", [(5000, 256), (4099, 200), (3000, 130), (2000, 64), (2500, 65), (1000, 17),
+                                 (70001, 256)])
+def test_tc_solve_matches_oracle(gpu_lib, n, m):
+    from paper_2405_10923_gb300 import torch_api as ta
+
+    k = max(2 * m, 64)
+    W = ri.gaussian(n, m, 90).astype(np.float32).astype(np.float64)
+    sk, osk = ta.Sketch(n, k, gpu_lib.SRHT, 91), sketch.SRHTSketch(n, k, 91)
+    out = ta.factor(sk, _dev(W), alg=gpu_lib.ALG_REC, passes=1)
+    torch.cuda.synchronize()
+    assert ta.info(out)["status"] == 0
+    Q, R = _np(out["Q"]), _np(out["R"])
+    # backward stable row solves: residual at float32 level
+    assert metrics.residual(W, Q, R) <= 1e-6
+    U, S, T, Ro, M = rhqr.rec_rhqr(W, osk)
+    assert np.max(np.abs(Q - rhqr.form_q(U, T))) <= 1e-4
+    assert metrics.sketch_orthogonality(Q, osk) <= 1e-5
+    sk.close()
+
+
+def test_tc_solve_in_place_refinement_high_condition(gpu_lib):
+    from paper_2405_10923_gb300 import torch_api as ta
+
+    n, m, k = 1 << 16, 256, 512
+    W = ri.spectrum(n, m, 1e8, 92).astype(np.float32).astype(np.float64)
+    sk, osk = ta.Sketch(n, k, gpu_lib.SRHT, 93), sketch.SRHTSketch(n, k, 93)
+    out = ta.factor(sk, _dev(W), alg=gpu_lib.ALG_REC, passes=3)
+    torch.cuda.synchronize()
+    assert ta.info(out)["passes_done"] == 3
+    Q, R = _np(out["Q"]), _np(out["R"])
+    assert metrics.residual(W, Q, R) <= 1e-5
+    assert metrics.sketch_orthogonality(Q, osk) <= 1e-5
+    sk.close()
