@@ -185,6 +185,27 @@ rhqr_status rhqr_reconstruct(rhqr_sketch s, const double *S, int64_t lds, const 
                              rhqr_stream_t stream);
 
 /*
+ * rhqr_sketch_apply_noalloc -- rhqr_sketch_apply (Algorithm 1) without a
+ * caller workspace; the paper has no counterpart.  For callers that cannot
+ * allocate device memory when they call: code running inside a CUDA-graph
+ * capture or a framework hook where cudaMalloc is forbidden or would break
+ * the capture, real-time paths that must not block on the allocator, and
+ * hosts that own all device memory and cannot hand the library a workspace.
+ * Arguments as for rhqr_sketch_apply (X and Z are still the caller's).
+ * Scratch: a fixed RHQR_NOALLOC_SCRATCH_BYTES device array inside the library
+ * that every GPU loading the library holds until the process exits; a call
+ * needing more scratch (large k * c) returns RHQR_ENOMEM and does nothing.
+ * The call allocates nothing.  Its first call on a device looks up the
+ * array's device address (with that device current), so make that first call
+ * before any stream capture.  All calls share the array, which keeps the last
+ * call's contents; calls whose work overlaps on the GPU (several streams or
+ * threads) race on it and must be serialised by the caller.
+ */
+#define RHQR_NOALLOC_SCRATCH_BYTES (24u * 1024u * 1024u)
+rhqr_status rhqr_sketch_apply_noalloc(rhqr_sketch s, int32_t m, const void *X, int32_t xt, int64_t n, int32_t c,
+                                      int64_t ldx, double *Z, int64_t ldz, rhqr_stream_t stream);
+
+/*
  * Instrumentation (no counterpart in the paper).
  * rhqr_launch_count: number of kernels this library has launched so far in the
  *   process (every launch site counts itself; host-side counter).

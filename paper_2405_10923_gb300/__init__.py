@@ -89,6 +89,7 @@ _SIGNATURES = {
                            _p, _i64, _p, _sz, _p, _p]),
     "rhqr_reconstruct": (_i32, [_p, _p, _i64, _p, _p, _p, _i64, _p, _i32, _i64, _i32, _i64, _p, _i64, _p, _i64, _p,
                                 _sz, _p]),
+    "rhqr_sketch_apply_noalloc": (_i32, [_p, _i32, _p, _i32, _i64, _i32, _i64, _p, _i64, _p]),
     "rhqr_launch_count": (_i64, []),
     "rhqr_profile_enable": (None, [_i32]),
     "rhqr_profile_read": (_i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
@@ -234,6 +235,11 @@ def rhqr_workspace_size(s: int, n: int, m: int, wt: int, opts: rhqr_opts | None 
 def rhqr_sketch_apply(s, m, X, xt, n, c, ldx, Z, ldz, ws, ws_bytes, stream=None) -> None:
     _check("rhqr_sketch_apply", load().rhqr_sketch_apply(s, m, _ptr(X), xt, n, c, ldx, _ptr(Z), ldz, _ptr(ws),
                                                          ws_bytes, _stream(stream)))
+
+
+def rhqr_sketch_apply_noalloc(s, m, X, xt, n, c, ldx, Z, ldz, stream=None) -> None:
+    _check("rhqr_sketch_apply_noalloc", load().rhqr_sketch_apply_noalloc(s, m, _ptr(X), xt, n, c, ldx, _ptr(Z), ldz,
+                                                                         _stream(stream)))
 
 
 def rhqr_factor(s, W, wt, n, m, ldw, opts, U, ldu, S, lds, T, R, Q, ldq, ws, ws_bytes, info, stream=None) -> None:

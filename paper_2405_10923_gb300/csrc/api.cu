@@ -24,6 +24,8 @@ struct rhqr_sketch_s {
 
 namespace rhqr {
 
+const SketchView *sketch_view_of(rhqr_sketch s) { return &s->view; }
+
 static const long long kDefaultBudget = 20000000LL;
 
 static bool valid_dtype_hd(int32_t t) { return t == RHQR_F64 || t == RHQR_F32; }
