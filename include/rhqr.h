@@ -185,6 +185,41 @@ rhqr_status rhqr_reconstruct(rhqr_sketch s, const double *S, int64_t lds, const 
                              rhqr_stream_t stream);
 
 /*
+ * RHQR-Arnoldi (Algorithm 7): the Krylov basis of an operator A is kept in
+ * compact form (U, S = Psi U, T) of mmax + 1 randomized reflectors, with
+ * Psi = diag(I_{mmax+1}, Omega) (Omega = columns mmax+1..n-1 of the sketch).
+ * The caller applies A: after begin(r0) gives q_1, every step(w = A q_j)
+ * returns the Hessenberg column h_j and the next basis vector q_{j+1}, so that
+ * A Q_m = Q_{m+1} H (eq. arnoldirelation) and Psi Q_{m+1} is orthonormal.
+ *   create : n rows, up to mmax steps, basis dtype F64 or F32, reflector
+ *            scaling 0 (unit diagonal) or 1 (||s|| = sqrt 2).  Allocates the
+ *            handle's device memory (n x (mmax+1) basis plus small arrays).
+ *            Requires mmax + 1 <= k and n > mmax + 1 (and n equal to the
+ *            sketch's n for a Gaussian sketch).
+ *   begin  : r0 = b - A x0 (n, device, basis dtype).  h0 (device, mmax + 1
+ *            float64) receives (-sigma_1 rho_1, 0, ...); q1 (device, n) the
+ *            first basis vector (may be NULL).
+ *   step   : w = A q_j (device, n).  h (device, mmax + 1 float64) receives
+ *            h_j; q_next (device, n, may be NULL) receives q_{j+1}.  At most
+ *            mmax steps after begin; more return RHQR_EINVAL.
+ *   export : copies U (n x (mmax+1), ldu), S ((k+mmax+1) x (mmax+1), lds),
+ *            T ((mmax+1) x (mmax+1)) to caller device buffers (any may be
+ *            NULL) and writes the number of reflectors taken to *count (host).
+ * Breakdown (rho = 0) and non-finite values are reported in the device info.
+ * Work is enqueued on `stream`; a handle serves one stream at a time.
+ */
+typedef struct rhqr_arnoldi_s *rhqr_arnoldi;
+rhqr_status rhqr_arnoldi_create(rhqr_sketch s, int64_t n, int32_t mmax, int32_t basis_dtype, int32_t scaling,
+                                rhqr_arnoldi *out);
+rhqr_status rhqr_arnoldi_destroy(rhqr_arnoldi a);
+rhqr_status rhqr_arnoldi_begin(rhqr_arnoldi a, const void *r0, double *h0, void *q1, rhqr_info *info,
+                               rhqr_stream_t stream);
+rhqr_status rhqr_arnoldi_step(rhqr_arnoldi a, const void *w, double *h, void *q_next, rhqr_info *info,
+                              rhqr_stream_t stream);
+rhqr_status rhqr_arnoldi_export(rhqr_arnoldi a, void *U, int64_t ldu, double *S, int64_t lds, double *T,
+                                int32_t *count, rhqr_stream_t stream);
+
+/*
  * rhqr_sketch_apply_noalloc -- rhqr_sketch_apply (Algorithm 1) without a
  * caller workspace; the paper has no counterpart.  For callers that cannot
  * allocate device memory when they call: code running inside a CUDA-graph

@@ -89,6 +89,11 @@ _SIGNATURES = {
                            _p, _i64, _p, _sz, _p, _p]),
     "rhqr_reconstruct": (_i32, [_p, _p, _i64, _p, _p, _p, _i64, _p, _i32, _i64, _i32, _i64, _p, _i64, _p, _i64, _p,
                                 _sz, _p]),
+    "rhqr_arnoldi_create": (_i32, [_p, _i64, _i32, _i32, _i32, ctypes.POINTER(_p)]),
+    "rhqr_arnoldi_destroy": (_i32, [_p]),
+    "rhqr_arnoldi_begin": (_i32, [_p, _p, _p, _p, _p, _p]),
+    "rhqr_arnoldi_step": (_i32, [_p, _p, _p, _p, _p, _p]),
+    "rhqr_arnoldi_export": (_i32, [_p, _p, _i64, _p, _i64, _p, ctypes.POINTER(_i32), _p]),
     "rhqr_sketch_apply_noalloc": (_i32, [_p, _i32, _p, _i32, _i64, _i32, _i64, _p, _i64, _p]),
     "rhqr_launch_count": (_i64, []),
     "rhqr_profile_enable": (None, [_i32]),
@@ -235,6 +240,33 @@ def rhqr_workspace_size(s: int, n: int, m: int, wt: int, opts: rhqr_opts | None 
 def rhqr_sketch_apply(s, m, X, xt, n, c, ldx, Z, ldz, ws, ws_bytes, stream=None) -> None:
     _check("rhqr_sketch_apply", load().rhqr_sketch_apply(s, m, _ptr(X), xt, n, c, ldx, _ptr(Z), ldz, _ptr(ws),
                                                          ws_bytes, _stream(stream)))
+
+
+def rhqr_arnoldi_create(s: int, n: int, mmax: int, basis_dtype: int = F64, scaling: int = 0) -> int:
+    out = _p()
+    _check("rhqr_arnoldi_create", load().rhqr_arnoldi_create(s, n, mmax, basis_dtype, scaling, ctypes.byref(out)))
+    return out.value
+
+
+def rhqr_arnoldi_destroy(a: int) -> None:
+    _check("rhqr_arnoldi_destroy", load().rhqr_arnoldi_destroy(a))
+
+
+def rhqr_arnoldi_begin(a, r0, h0, q1, info, stream=None) -> None:
+    _check("rhqr_arnoldi_begin", load().rhqr_arnoldi_begin(a, _ptr(r0), _ptr(h0), _ptr(q1), _ptr(info),
+                                                           _stream(stream)))
+
+
+def rhqr_arnoldi_step(a, w, h, q_next, info, stream=None) -> None:
+    _check("rhqr_arnoldi_step", load().rhqr_arnoldi_step(a, _ptr(w), _ptr(h), _ptr(q_next), _ptr(info),
+                                                         _stream(stream)))
+
+
+def rhqr_arnoldi_export(a, U=None, ldu=0, S=None, lds=0, T=None, stream=None) -> int:
+    cnt = _i32()
+    _check("rhqr_arnoldi_export", load().rhqr_arnoldi_export(a, _ptr(U), ldu, _ptr(S), lds, _ptr(T),
+                                                             ctypes.byref(cnt), _stream(stream)))
+    return cnt.value
 
 
 def rhqr_sketch_apply_noalloc(s, m, X, xt, n, c, ldx, Z, ldz, stream=None) -> None:

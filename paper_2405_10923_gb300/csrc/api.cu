@@ -22,6 +22,11 @@ struct rhqr_sketch_s {
   size_t mem_bytes;
 };
 
+struct rhqr_arnoldi_s {
+  rhqr::ArnoldiState st;
+  void *mem;
+};
+
 namespace rhqr {
 
 const SketchView *sketch_view_of(rhqr_sketch s) { return &s->view; }
@@ -499,6 +504,86 @@ rhqr_status rhqr_reconstruct(rhqr_sketch s, const double *S, int64_t lds, const 
     RHQR_TRY(top_from_s<float>(S, lds, m, (float *)U, ldu, st));
     if (Q) RHQR_TRY(rows_form_q<float>((const float *)U, ldu, 0, m, m, (const float *)GT, (float *)Q, ldq, st));
   }
+  return RHQR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// RHQR-Arnoldi
+// ---------------------------------------------------------------------------
+
+rhqr_status rhqr_arnoldi_create(rhqr_sketch s, int64_t n, int32_t mmax, int32_t basis_dtype, int32_t scaling,
+                                rhqr_arnoldi *out) {
+  if (out == nullptr) return RHQR_EINVAL;
+  *out = nullptr;
+  if (s == nullptr || mmax < 1 || !valid_dtype_hd(basis_dtype) || (scaling != 0 && scaling != 1))
+    return RHQR_EINVAL;
+  const int32_t M = mmax + 1;
+  if (M > 1024) return RHQR_ENOTSUP;
+  RHQR_TRY(check_sketch_shape(s->view, n, M));
+  rhqr_arnoldi a = new (std::nothrow) rhqr_arnoldi_s();
+  if (a == nullptr) return RHQR_ENOMEM;
+  a->st.view = s->view;
+  a->st.n = n;
+  a->st.M = M;
+  a->st.dtype = basis_dtype;
+  a->st.scaling = scaling;
+  a->st.j = 0;
+  size_t bytes = arnoldi_state_bytes(s->view, n, M, basis_dtype);
+  if (cudaMalloc(&a->mem, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete a;
+    return RHQR_ENOMEM;
+  }
+  if (arnoldi_carve(a->st, a->mem, bytes) != RHQR_OK) {
+    cudaFree(a->mem);
+    delete a;
+    return RHQR_ENOMEM;
+  }
+  *out = a;
+  return RHQR_OK;
+}
+
+rhqr_status rhqr_arnoldi_destroy(rhqr_arnoldi a) {
+  if (a == nullptr) return RHQR_OK;
+  cudaError_t e = cudaFree(a->mem);
+  delete a;
+  return e == cudaSuccess ? RHQR_OK : RHQR_ECUDA;
+}
+
+rhqr_status rhqr_arnoldi_begin(rhqr_arnoldi a, const void *r0, double *h0, void *q1, rhqr_info *info,
+                               rhqr_stream_t stream) {
+  if (a == nullptr || r0 == nullptr || h0 == nullptr || info == nullptr) return RHQR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  RHQR_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(rhqr_info), st));
+  return arnoldi_begin(a->st, r0, h0, q1, info, st);
+}
+
+rhqr_status rhqr_arnoldi_step(rhqr_arnoldi a, const void *w, double *h, void *q_next, rhqr_info *info,
+                              rhqr_stream_t stream) {
+  if (a == nullptr || w == nullptr || h == nullptr || info == nullptr) return RHQR_EINVAL;
+  if (a->st.j < 1 || a->st.j >= a->st.M) return RHQR_EINVAL;
+  return arnoldi_step(a->st, w, h, q_next, info, (cudaStream_t)stream);
+}
+
+rhqr_status rhqr_arnoldi_export(rhqr_arnoldi a, void *U, int64_t ldu, double *S, int64_t lds, double *T,
+                                int32_t *count, rhqr_stream_t stream) {
+  if (a == nullptr) return RHQR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const ArnoldiState &A = a->st;
+  const int64_t p = (int64_t)A.view.k + A.M;
+  size_t es = dtype_size(A.dtype);
+  if (U != nullptr) {
+    if (ldu < A.n) return RHQR_EINVAL;
+    RHQR_CUDA_TRY(cudaMemcpy2DAsync(U, ldu * es, A.U, A.ldu * es, A.n * es, A.M, cudaMemcpyDeviceToDevice, st));
+    RHQR_TRY(arnoldi_scale_copy(A, U, ldu, st));
+  }
+  if (S != nullptr) {
+    if (lds < p) return RHQR_EINVAL;
+    RHQR_CUDA_TRY(cudaMemcpy2DAsync(S, lds * 8, A.S, A.lds * 8, p * 8, A.M, cudaMemcpyDeviceToDevice, st));
+  }
+  if (T != nullptr)
+    RHQR_CUDA_TRY(cudaMemcpyAsync(T, A.T, sizeof(double) * A.M * A.M, cudaMemcpyDeviceToDevice, st));
+  if (count != nullptr) *count = A.j;
   return RHQR_OK;
 }
 

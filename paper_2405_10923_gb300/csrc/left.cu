@@ -378,4 +378,205 @@ rhqr_status left_factor(const SketchView &s, const void *W, int32_t wt, int64_t 
   return RHQR_ENOTSUP;
 }
 
+// ---------------------------------------------------------------------------
+// RHQR-Arnoldi (Algorithm 7) on the same kernels
+// ---------------------------------------------------------------------------
+
+// coef_l = sum_{i >= l} T[l, i] S[j, i] for l <= j (x = T_{j+1} S_{j+1}^t e_j),
+// the last one divided by gamma_j (column j of U is stored unscaled).
+__global__ void arnoldi_coef_kernel(const double *T, int32_t M, const double *S, int64_t lds, int32_t j,
+                                    const double *gamma, int32_t unit, double *coef) {
+  for (int l = threadIdx.x; l <= j; l += blockDim.x) {
+    double acc = 0.0;
+    for (int i = l; i <= j; ++i) acc += T[(int64_t)i * M + l] * S[(int64_t)i * lds + j];
+    if (l == j) acc = acc / gamma[j];
+    coef[l] = acc;
+  }
+  (void)unit;
+}
+
+// q = e_j - U[:, 0..j] coef over all n rows; column j of U is unscaled except
+// rows <= j (zeros above, gamma at j), so row j gives exactly 1 - coef_j gamma_j / gamma_j.
+template <class T>
+__global__ void arnoldi_q_kernel(const T *U, int64_t ldu, int64_t n, int32_t j, const double *coef, T *q) {
+  __shared__ double c_s[1024];
+  for (int l = threadIdx.x; l <= j; l += blockDim.x) c_s[l] = coef[l];
+  __syncthreads();
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = (i == j) ? 1.0 : 0.0;
+  for (int l = 0; l <= j; ++l) acc -= (double)U[(int64_t)l * ldu + i] * c_s[l];
+  q[i] = (T)acc;
+}
+
+size_t arnoldi_state_bytes(const SketchView &s, int64_t n, int32_t M, int32_t dt) {
+  Carver c(nullptr, 0);
+  const int64_t p = (int64_t)s.k + M;
+  c.take<char>((size_t)n * M * dtype_size(dt));  // U
+  c.take<double>((size_t)p * M);                  // S
+  c.take<double>((size_t)M * M);                  // T
+  c.take<double>(8 * (size_t)M + 2 * p);          // beta gamma c v d coef y z
+  c.take<int>(4);
+  if (s.kind == RHQR_SKETCH_SRHT) c.take<char>((size_t)s.N1 * s.d2 * dtype_size(dt));
+  else c.take<double>((size_t)ceil_div(n, LG_RB) * s.k);
+  c.take<char>(sketch_apply_workspace_bytes(s, M, dt, n, 1));
+  return c.used() + 1024;
+}
+
+rhqr_status arnoldi_carve(ArnoldiState &a, void *mem, size_t bytes) {
+  Carver c(mem, bytes);
+  const int64_t p = (int64_t)a.view.k + a.M;
+  a.U = c.take<char>((size_t)a.n * a.M * dtype_size(a.dtype));
+  a.ldu = a.n;
+  a.S = c.take<double>((size_t)p * a.M);
+  a.lds = p;
+  a.T = c.take<double>((size_t)a.M * a.M);
+  double *vecs = c.take<double>(8 * (size_t)a.M + 2 * p);
+  a.beta = vecs;
+  a.gamma = vecs + a.M;
+  a.c = vecs + 2 * a.M;
+  a.v = vecs + 3 * a.M;
+  a.d = vecs + 4 * a.M;
+  a.coef = vecs + 5 * a.M;
+  a.y = vecs + 8 * a.M;
+  a.z = vecs + 8 * a.M + p;
+  a.stop = c.take<int>(4);
+  if (a.view.kind == RHQR_SKETCH_SRHT) {
+    a.stage_bytes = (size_t)a.view.N1 * a.view.d2 * dtype_size(a.dtype);
+  } else {
+    a.stage_bytes = (size_t)ceil_div(a.n, LG_RB) * a.view.k * sizeof(double);
+  }
+  a.stage = c.take<char>(a.stage_bytes);
+  a.aws_bytes = sketch_apply_workspace_bytes(a.view, a.M, a.dtype, a.n, 1);
+  a.aws = c.take<char>(a.aws_bytes);
+  return c.overflow() ? RHQR_ENOMEM : RHQR_OK;
+}
+
+// refresh `w` with the reflectors 0..J-1 (coefficients in a.c), store it as
+// column J of U, sketch it into a.y (fused), then take reflector J.
+template <class T>
+static rhqr_status arnoldi_reflect(ArnoldiState &a, const T *w, double *h, rhqr_info *info, cudaStream_t st) {
+  const int32_t J = a.j, M = a.M;
+  const int64_t p = (int64_t)a.view.k + M;
+  // the column kernel reads W[J * ldw + i]: present w as column J of a virtual matrix
+  const T *Wbase = w - (int64_t)J * a.n;
+  ColArgs ca{Wbase, a.n, a.U, a.ldu, a.n, M, J, a.c, a.gamma, a.y, a.scaling == 0 ? 1 : 0};
+  const double scale = 1.0 / sqrt((double)a.view.k);
+  if (a.view.kind == RHQR_SKETCH_SRHT) {
+    size_t smem = (size_t)a.view.N2 * sizeof(T);
+    if (smem > 48 * 1024)
+      RHQR_CUDA_TRY(
+          cudaFuncSetAttribute(left_column_srht_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    left_column_srht_kernel<T><<<a.view.N1, 512, smem, st>>>(ca, a.view.sign_bits, a.view.N2, a.view.i2_list,
+                                                              a.view.d2, (T *)a.stage);
+    RHQR_LAUNCH_CHECK();
+    left_srht_combine_kernel<T><<<(unsigned)ceil_div(a.view.k, 128), 128, 0, st>>>(
+        (const T *)a.stage, a.view.N1, a.view.d2, a.view.sample_i1, a.view.sample_slot, a.view.k, M, scale, a.y);
+    RHQR_LAUNCH_CHECK();
+  } else {
+    int nb = (int)ceil_div(a.n, LG_RB);
+    switch (a.view.omega_dtype) {
+      case RHQR_F64:
+        left_column_gauss_kernel<T, double><<<nb, LG_RB, 0, st>>>(ca, (const double *)a.view.G, a.view.ldg, a.view.k,
+                                                                  (double *)a.stage);
+        break;
+      case RHQR_F32:
+        left_column_gauss_kernel<T, float><<<nb, LG_RB, 0, st>>>(ca, (const float *)a.view.G, a.view.ldg, a.view.k,
+                                                                 (double *)a.stage);
+        break;
+      case RHQR_BF16:
+        left_column_gauss_kernel<T, __nv_bfloat16><<<nb, LG_RB, 0, st>>>(
+            ca, (const __nv_bfloat16 *)a.view.G, a.view.ldg, a.view.k, (double *)a.stage);
+        break;
+      default:
+        left_column_gauss_kernel<T, __half><<<nb, LG_RB, 0, st>>>(ca, (const __half *)a.view.G, a.view.ldg, a.view.k,
+                                                                  (double *)a.stage);
+        break;
+    }
+    RHQR_LAUNCH_CHECK();
+    left_gauss_reduce_kernel<<<(unsigned)ceil_div(a.view.k, 128), 128, 0, st>>>((const double *)a.stage, nb,
+                                                                               a.view.k, M, scale, a.y);
+    RHQR_LAUNCH_CHECK();
+  }
+  // RHVector at column J; its "R column" is the Hessenberg column h (M entries)
+  left_rhvector_kernel<T><<<1, 256, 0, st>>>(a.y, p, M, J, a.scaling, a.S, a.lds, h - (int64_t)J * M, a.beta,
+                                             a.gamma, (T *)a.U, a.ldu, info, a.stop);
+  RHQR_LAUNCH_CHECK();
+  // column J of T: t_J = (-beta T_J S_J^t s_J; beta)
+  {
+    dim3 g((unsigned)std::max(1, J), 2);
+    left_dots_kernel<<<g, 256, 0, st>>>(a.S, a.lds, p, J, J, a.z, 0, a.d, a.v);
+    RHQR_LAUNCH_CHECK();
+    left_tcol_coef_kernel<<<1, 256, 0, st>>>(a.T, M, J, a.beta, a.d, a.v, 0, a.c);
+    RHQR_LAUNCH_CHECK();
+  }
+  a.j = J + 1;
+  return RHQR_OK;
+}
+
+// q_J = e_J - U_{J+1} T_{J+1} S_{J+1}^t e_J  (J = the newest reflector)
+template <class T>
+static rhqr_status arnoldi_basis(ArnoldiState &a, T *q, cudaStream_t st) {
+  const int32_t J = a.j - 1;
+  arnoldi_coef_kernel<<<1, 256, 0, st>>>(a.T, a.M, a.S, a.lds, J, a.gamma, a.scaling == 0, a.coef);
+  RHQR_LAUNCH_CHECK();
+  arnoldi_q_kernel<T><<<(unsigned)ceil_div(a.n, 256), 256, 0, st>>>((const T *)a.U, a.ldu, a.n, J, a.coef, q);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
+}
+
+template <class T>
+static rhqr_status arnoldi_begin_t(ArnoldiState &a, const T *r0, double *h0, T *q1, rhqr_info *info,
+                                   cudaStream_t st) {
+  a.j = 0;
+  RHQR_CUDA_TRY(cudaMemsetAsync(a.stop, 0, 4 * sizeof(int), st));
+  RHQR_CUDA_TRY(cudaMemsetAsync(a.T, 0, sizeof(double) * a.M * a.M, st));
+  RHQR_TRY(arnoldi_reflect<T>(a, r0, h0, info, st));
+  if (q1 != nullptr) RHQR_TRY(arnoldi_basis<T>(a, q1, st));
+  return RHQR_OK;
+}
+
+template <class T>
+static rhqr_status arnoldi_step_t(ArnoldiState &a, const T *w, double *h, T *qn, rhqr_info *info, cudaStream_t st) {
+  const int32_t J = a.j;
+  const int64_t p = (int64_t)a.view.k + a.M;
+  // z = Psi w (the sketch of A q_j), then c = T_J^t S_J^t z
+  RHQR_TRY(sketch_apply_simt(a.view, a.M, w, sizeof(T) == 8 ? RHQR_F64 : RHQR_F32, a.n, 1, a.n, a.z, p, a.aws,
+                             a.aws_bytes, st));
+  dim3 g((unsigned)J, 2);
+  left_dots_kernel<<<g, 256, 0, st>>>(a.S, a.lds, p, 0, 0, a.z, J, a.d, a.v);
+  RHQR_LAUNCH_CHECK();
+  left_tcol_coef_kernel<<<1, 256, 0, st>>>(a.T, a.M, -1, a.beta, a.d, a.v, J, a.c);
+  RHQR_LAUNCH_CHECK();
+  RHQR_TRY(arnoldi_reflect<T>(a, w, h, info, st));
+  if (qn != nullptr) RHQR_TRY(arnoldi_basis<T>(a, qn, st));
+  return RHQR_OK;
+}
+
+// the newest column of U is stored unscaled (deferred scaling): scale it in a copy
+rhqr_status arnoldi_scale_copy(const ArnoldiState &a, void *Udst, int64_t ldu, cudaStream_t st) {
+  if (a.j < 1) return RHQR_OK;
+  if (a.dtype == RHQR_F64)
+    left_scale_last_kernel<double><<<(unsigned)ceil_div(a.n, 256), 256, 0, st>>>((double *)Udst, ldu, a.n, a.j - 1,
+                                                                                 a.gamma, a.scaling == 0);
+  else
+    left_scale_last_kernel<float><<<(unsigned)ceil_div(a.n, 256), 256, 0, st>>>((float *)Udst, ldu, a.n, a.j - 1,
+                                                                                a.gamma, a.scaling == 0);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
+}
+
+rhqr_status arnoldi_begin(ArnoldiState &a, const void *r0, double *h0, void *q1, rhqr_info *info,
+                          cudaStream_t st) {
+  if (a.dtype == RHQR_F64)
+    return arnoldi_begin_t<double>(a, (const double *)r0, h0, (double *)q1, info, st);
+  return arnoldi_begin_t<float>(a, (const float *)r0, h0, (float *)q1, info, st);
+}
+
+rhqr_status arnoldi_step(ArnoldiState &a, const void *w, double *h, void *qn, rhqr_info *info, cudaStream_t st) {
+  if (a.j < 1 || a.j >= a.M) return RHQR_EINVAL;
+  if (a.dtype == RHQR_F64) return arnoldi_step_t<double>(a, (const double *)w, h, (double *)qn, info, st);
+  return arnoldi_step_t<float>(a, (const float *)w, h, (float *)qn, info, st);
+}
+
 }  // namespace rhqr

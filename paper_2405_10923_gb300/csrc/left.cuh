@@ -11,4 +11,28 @@ rhqr_status left_factor(const SketchView &s, const void *W, int32_t wt, int64_t 
                         int32_t scaling, void *U, int64_t ldu, double *S, int64_t lds, double *T, double *R, void *Q,
                         int64_t ldq, void *ws, size_t ws_bytes, rhqr_info *info, cudaStream_t st);
 
+// State of one RHQR-Arnoldi process (Algorithm 7): M = mmax + 1 reflectors in
+// compact form (U n x M in the basis dtype, S = Psi U, T), Psi = diag(I_M, Omega).
+struct ArnoldiState {
+  SketchView view;
+  int64_t n;
+  int32_t M, dtype, scaling, j;
+  void *U;
+  int64_t ldu;
+  double *S;
+  int64_t lds;
+  double *T, *beta, *gamma, *c, *v, *d, *coef, *y, *z;
+  int *stop;
+  void *stage;
+  size_t stage_bytes;
+  void *aws;
+  size_t aws_bytes;
+};
+
+size_t arnoldi_state_bytes(const SketchView &s, int64_t n, int32_t M, int32_t dt);
+rhqr_status arnoldi_carve(ArnoldiState &a, void *mem, size_t bytes);
+rhqr_status arnoldi_begin(ArnoldiState &a, const void *r0, double *h0, void *q1, rhqr_info *info, cudaStream_t st);
+rhqr_status arnoldi_scale_copy(const ArnoldiState &a, void *Udst, int64_t ldu, cudaStream_t st);
+rhqr_status arnoldi_step(ArnoldiState &a, const void *w, double *h, void *qn, rhqr_info *info, cudaStream_t st);
+
 }  // namespace rhqr

@@ -7,11 +7,12 @@ from __future__ import annotations
 import torch
 
 from . import (ALG_LEFT, ALG_REC, BF16, F16, F32, F64, GAUSSIAN, SRHT, colmajor, dtype_code, ld_of, read_info,
+               rhqr_arnoldi_begin, rhqr_arnoldi_create, rhqr_arnoldi_destroy, rhqr_arnoldi_export, rhqr_arnoldi_step,
                rhqr_default_opts, rhqr_factor, rhqr_reconstruct, rhqr_sketch_apply, rhqr_sketch_apply_workspace,
                rhqr_sketch_create, rhqr_sketch_destroy, rhqr_sketch_export, rhqr_sketch_shape, rhqr_workspace_size)
 
 TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}
-__all__ = ["Sketch", "factor", "reconstruct", "colmajor", "ALG_LEFT", "ALG_REC", "GAUSSIAN", "SRHT"]
+__all__ = ["Sketch", "Arnoldi", "factor", "reconstruct", "colmajor", "ALG_LEFT", "ALG_REC", "GAUSSIAN", "SRHT"]
 
 
 class Sketch:
@@ -112,3 +113,43 @@ def reconstruct(sk: Sketch, S, T, R, Z, W, want_Q=True):
 
 def info(out) -> dict:
     return read_info(out["info"])
+
+
+class Arnoldi:
+    """Owner of an rhqr_arnoldi handle (Algorithm 7 with a caller-applied operator)."""
+
+    def __init__(self, sk: Sketch, n: int, mmax: int, dtype=torch.float64, scaling: int = 0, device="cuda"):
+        self.n, self.mmax, self.M, self.dtype, self.device = n, mmax, mmax + 1, dtype, device
+        self.k = sk.k
+        self.handle = rhqr_arnoldi_create(sk.handle, n, mmax, dtype_code(torch.empty(0, dtype=dtype)), scaling)
+        self.info = torch.zeros(4, dtype=torch.int32, device=device)
+
+    def close(self):
+        if self.handle:
+            rhqr_arnoldi_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def begin(self, r0: torch.Tensor):
+        h0 = torch.zeros(self.M, dtype=torch.float64, device=self.device)
+        q = torch.zeros(self.n, dtype=self.dtype, device=self.device)
+        rhqr_arnoldi_begin(self.handle, r0, h0, q, self.info)
+        return h0, q
+
+    def step(self, w: torch.Tensor):
+        h = torch.zeros(self.M, dtype=torch.float64, device=self.device)
+        q = torch.zeros(self.n, dtype=self.dtype, device=self.device)
+        rhqr_arnoldi_step(self.handle, w, h, q, self.info)
+        return h, q
+
+    def export(self):
+        U = colmajor(torch.zeros((self.n, self.M), dtype=self.dtype, device=self.device))
+        S = colmajor(torch.zeros((self.k + self.M, self.M), dtype=torch.float64, device=self.device))
+        T = torch.zeros((self.M, self.M), dtype=torch.float64, device=self.device)
+        cnt = rhqr_arnoldi_export(self.handle, U, ld_of(U), S, ld_of(S), T)
+        return U, S, T.t(), cnt

@@ -112,3 +112,22 @@ def device_gaussian(n: int, m: int, seed: int, dtype=None, device="cuda"):
     out = torch.empty((m, n), dtype=dtype, device=device).t()
     out.copy_(torch.randn((n, m), generator=g, dtype=torch.float64, device=device))
     return out
+
+
+# ---------------------------------------------------------------------------
+# 2-D convection-diffusion operator (the GMRES workload), matrix-free
+# ---------------------------------------------------------------------------
+
+
+def stencil_apply(u, g: int, peclet: float = 10.0):
+    """A u for -Laplace(u) + Pe (u_x + u_y) on the unit square, g x g interior
+    points, h = 1/(g+1), zero Dirichlet boundary, central differences, scaled by
+    h^2.  `u` is a numpy array or torch tensor of length g*g (row-major grid)."""
+    c = peclet / (2.0 * (g + 1))  # Pe h / 2
+    U = u.reshape(g, g)
+    out = 4.0 * U
+    out[1:, :] += -U[:-1, :] - c * U[:-1, :]
+    out[:-1, :] += -U[1:, :] + c * U[1:, :]
+    out[:, 1:] += -U[:, :-1] - c * U[:, :-1]
+    out[:, :-1] += -U[:, 1:] + c * U[:, 1:]
+    return out.reshape(-1)
