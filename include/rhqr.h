@@ -220,6 +220,52 @@ rhqr_status rhqr_arnoldi_export(rhqr_arnoldi a, void *U, int64_t ldu, double *S,
                                 int32_t *count, rhqr_stream_t stream);
 
 /*
+ * Batched recRHQR (Algorithm 6 with the refinement passes of rhqr_factor) of
+ * `count` independent tall-skinny problems W_i (n_i x m_i) with SRHT sketches
+ * s[i] (the paper factors one matrix; the batch runs many uneven ones at once).
+ *   create : binds, once, the problems' sketches, shapes and device pointers
+ *            (host arrays of `count` entries; every pointer they hold is a
+ *            device pointer owned by the caller and must stay valid while the
+ *            plan is used).  W_i: n_i x m_i, dtype wt (F64 or F32), ldw_i >=
+ *            n_i; Q_i: n_i x m_i, dtype wt, ldq_i >= n_i (output, may alias
+ *            nothing else); S_i: (k_i+m_i) x m_i float64, lds_i >= k_i+m_i;
+ *            T_i, R_i: m_i x m_i float64 (ld = m_i).  opts: passes and scaling
+ *            as for rhqr_factor (NULL = defaults; alg, limbs and want_* are
+ *            ignored).  Requires 1 <= m_i <= 128, m_i < n_i <= N_i, m_i <= k_i
+ *            and an SRHT sketch per problem.  Allocates the plan (a host
+ *            object plus one device table) and synchronises the device.
+ *   workspace_size : device workspace bytes of rhqr_factor_batched.
+ *   rhqr_factor_batched : enqueues the whole batch on `stream` -- per pass one
+ *            launch per phase covering every problem (SRHT stage A, stage B,
+ *            FP64 Householder QR of each sketch, R accumulation, row solves
+ *            Q = X R^{-1}), then one launch writing S, T (Woodbury form), R
+ *            and the info records.  It allocates nothing, does not synchronise
+ *            and launches a fixed sequence, so it may be captured into a CUDA
+ *            graph and replayed as one graph launch while the bound pointers
+ *            and the plan stay unchanged.  info: `count` device rhqr_info
+ *            records, one per problem.  One plan serves one stream at a time.
+ *   tune   : times the candidate launch shapes (stage-A threads, solve rows per
+ *            block, solve grid cap) on the bound problems, `reps` launches
+ *            each, keeps the fastest in the plan and writes them to choice
+ *            (host, 3 int32; may be NULL).  It runs the batch first and
+ *            overwrites the outputs; it synchronises the stream (do not
+ *            capture it).  get/set_tuning read or restore a choice (set
+ *            rejects values outside the candidate lists with RHQR_EINVAL).
+ */
+typedef struct rhqr_batch_s *rhqr_batch;
+rhqr_status rhqr_batch_create(int32_t count, const rhqr_sketch *s, const void *const *W, int32_t wt,
+                              const int64_t *n, const int32_t *m, const int64_t *ldw, const rhqr_opts *opts,
+                              void *const *Q, const int64_t *ldq, double *const *S, const int64_t *lds,
+                              double *const *T, double *const *R, rhqr_batch *out);
+rhqr_status rhqr_batch_workspace_size(rhqr_batch b, size_t *bytes);
+rhqr_status rhqr_batch_destroy(rhqr_batch b);
+rhqr_status rhqr_factor_batched(rhqr_batch b, void *ws, size_t ws_bytes, rhqr_info *info, rhqr_stream_t stream);
+rhqr_status rhqr_batch_tune(rhqr_batch b, void *ws, size_t ws_bytes, rhqr_info *info, int32_t reps,
+                            int32_t *choice, rhqr_stream_t stream);
+rhqr_status rhqr_batch_get_tuning(rhqr_batch b, int32_t *choice /* host, 3 */);
+rhqr_status rhqr_batch_set_tuning(rhqr_batch b, const int32_t *choice /* host, 3 */);
+
+/*
  * rhqr_sketch_apply_noalloc -- rhqr_sketch_apply (Algorithm 1) without a
  * caller workspace; the paper has no counterpart.  For callers that cannot
  * allocate device memory when they call: code running inside a CUDA-graph

@@ -95,6 +95,14 @@ _SIGNATURES = {
     "rhqr_arnoldi_step": (_i32, [_p, _p, _p, _p, _p, _p]),
     "rhqr_arnoldi_export": (_i32, [_p, _p, _i64, _p, _i64, _p, ctypes.POINTER(_i32), _p]),
     "rhqr_sketch_apply_noalloc": (_i32, [_p, _i32, _p, _i32, _i64, _i32, _i64, _p, _i64, _p]),
+    "rhqr_batch_create": (_i32, [_i32, _p, _p, _i32, _p, _p, _p, ctypes.POINTER(rhqr_opts), _p, _p, _p, _p, _p, _p,
+                                 ctypes.POINTER(_p)]),
+    "rhqr_batch_workspace_size": (_i32, [_p, ctypes.POINTER(_sz)]),
+    "rhqr_batch_destroy": (_i32, [_p]),
+    "rhqr_factor_batched": (_i32, [_p, _p, _sz, _p, _p]),
+    "rhqr_batch_tune": (_i32, [_p, _p, _sz, _p, _i32, _p, _p]),
+    "rhqr_batch_get_tuning": (_i32, [_p, _p]),
+    "rhqr_batch_set_tuning": (_i32, [_p, _p]),
     "rhqr_launch_count": (_i64, []),
     "rhqr_profile_enable": (None, [_i32]),
     "rhqr_profile_read": (_i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
@@ -272,6 +280,54 @@ def rhqr_arnoldi_export(a, U=None, ldu=0, S=None, lds=0, T=None, stream=None) ->
 def rhqr_sketch_apply_noalloc(s, m, X, xt, n, c, ldx, Z, ldz, stream=None) -> None:
     _check("rhqr_sketch_apply_noalloc", load().rhqr_sketch_apply_noalloc(s, m, _ptr(X), xt, n, c, ldx, _ptr(Z), ldz,
                                                                          _stream(stream)))
+
+
+def _arr(ctype, values):
+    return (ctype * len(values))(*values)
+
+
+def rhqr_batch_create(sketches, W, wt, n, m, ldw, opts, Q, ldq, S, lds, T, R) -> int:
+    """Plan over len(sketches) problems; every list holds one entry per problem
+    (handles, ints, or tensors whose data pointers are taken)."""
+    cnt = len(sketches)
+    out = _p()
+    _check("rhqr_batch_create", load().rhqr_batch_create(
+        cnt, _arr(_p, sketches), _arr(_p, [_ptr(x) for x in W]), wt, _arr(_i64, n), _arr(_i32, m), _arr(_i64, ldw),
+        ctypes.byref(opts) if opts else None, _arr(_p, [_ptr(x) for x in Q]), _arr(_i64, ldq),
+        _arr(_p, [_ptr(x) for x in S]), _arr(_i64, lds), _arr(_p, [_ptr(x) for x in T]),
+        _arr(_p, [_ptr(x) for x in R]), ctypes.byref(out)))
+    return out.value
+
+
+def rhqr_batch_workspace_size(b: int) -> int:
+    out = _sz()
+    _check("rhqr_batch_workspace_size", load().rhqr_batch_workspace_size(b, ctypes.byref(out)))
+    return out.value
+
+
+def rhqr_batch_destroy(b: int) -> None:
+    _check("rhqr_batch_destroy", load().rhqr_batch_destroy(b))
+
+
+def rhqr_factor_batched(b, ws, ws_bytes, info, stream=None) -> None:
+    _check("rhqr_factor_batched", load().rhqr_factor_batched(b, _ptr(ws), ws_bytes, _ptr(info), _stream(stream)))
+
+
+def rhqr_batch_tune(b, ws, ws_bytes, info, reps=3, stream=None) -> tuple:
+    choice = (_i32 * 3)()
+    _check("rhqr_batch_tune", load().rhqr_batch_tune(b, _ptr(ws), ws_bytes, _ptr(info), reps, choice,
+                                                     _stream(stream)))
+    return tuple(choice)
+
+
+def rhqr_batch_get_tuning(b) -> tuple:
+    choice = (_i32 * 3)()
+    _check("rhqr_batch_get_tuning", load().rhqr_batch_get_tuning(b, choice))
+    return tuple(choice)
+
+
+def rhqr_batch_set_tuning(b, choice) -> None:
+    _check("rhqr_batch_set_tuning", load().rhqr_batch_set_tuning(b, _arr(_i32, list(choice))))
 
 
 def rhqr_factor(s, W, wt, n, m, ldw, opts, U, ldu, S, lds, T, R, Q, ldq, ws, ws_bytes, info, stream=None) -> None:

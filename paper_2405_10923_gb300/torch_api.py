@@ -4,15 +4,19 @@ arithmetic of the method happens here."""
 
 from __future__ import annotations
 
+import json
+import os
+
 import torch
 
 from . import (ALG_LEFT, ALG_REC, BF16, F16, F32, F64, GAUSSIAN, SRHT, colmajor, dtype_code, ld_of, read_info,
-               rhqr_arnoldi_begin, rhqr_arnoldi_create, rhqr_arnoldi_destroy, rhqr_arnoldi_export, rhqr_arnoldi_step,
+               rhqr_batch_create, rhqr_batch_destroy, rhqr_batch_get_tuning, rhqr_batch_set_tuning, rhqr_batch_tune,
+               rhqr_batch_workspace_size, rhqr_factor_batched, rhqr_arnoldi_begin, rhqr_arnoldi_create, rhqr_arnoldi_destroy, rhqr_arnoldi_export, rhqr_arnoldi_step,
                rhqr_default_opts, rhqr_factor, rhqr_reconstruct, rhqr_sketch_apply, rhqr_sketch_apply_workspace,
                rhqr_sketch_create, rhqr_sketch_destroy, rhqr_sketch_export, rhqr_sketch_shape, rhqr_workspace_size)
 
 TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}
-__all__ = ["Sketch", "Arnoldi", "factor", "reconstruct", "colmajor", "ALG_LEFT", "ALG_REC", "GAUSSIAN", "SRHT"]
+__all__ = ["Sketch", "Arnoldi", "Batch", "factor", "reconstruct", "colmajor", "ALG_LEFT", "ALG_REC", "GAUSSIAN", "SRHT"]
 
 
 class Sketch:
@@ -153,3 +157,87 @@ class Arnoldi:
         T = torch.zeros((self.M, self.M), dtype=torch.float64, device=self.device)
         cnt = rhqr_arnoldi_export(self.handle, U, ld_of(U), S, ld_of(S), T)
         return U, S, T.t(), cnt
+
+
+class Batch:
+    """Owner of an rhqr_batch plan over ragged problems (W_i column-major,
+    one SRHT Sketch each) and of its outputs Q_i, S_i, T_i, R_i, the per-problem
+    info records and the workspace."""
+
+    def __init__(self, sketches, Ws, opts=None, **kw):
+        self.sketches = list(sketches)
+        self.W = list(Ws)
+        self.opts = opts or make_opts(**kw)
+        dev = self.W[0].device
+        wt = dtype_code(self.W[0])
+        self.Q = [colmajor(torch.zeros(w.shape, dtype=w.dtype, device=dev)) for w in self.W]
+        self.S = [colmajor(torch.zeros((sk.k + w.shape[1], w.shape[1]), dtype=torch.float64, device=dev))
+                  for sk, w in zip(self.sketches, self.W)]
+        self.T = [colmajor(torch.zeros((w.shape[1], w.shape[1]), dtype=torch.float64, device=dev)) for w in self.W]
+        self.R = [colmajor(torch.zeros((w.shape[1], w.shape[1]), dtype=torch.float64, device=dev)) for w in self.W]
+        self.info = torch.zeros((len(self.W), 4), dtype=torch.int32, device=dev)
+        self.handle = rhqr_batch_create([sk.handle for sk in self.sketches], self.W, wt,
+                                        [w.shape[0] for w in self.W], [w.shape[1] for w in self.W],
+                                        [ld_of(w) for w in self.W], self.opts, self.Q, [ld_of(q) for q in self.Q],
+                                        self.S, [ld_of(x) for x in self.S], self.T, self.R)
+        self.ws_bytes = rhqr_batch_workspace_size(self.handle)
+        self.ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=dev)
+
+    def close(self):
+        if self.handle:
+            rhqr_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, stream=None):
+        rhqr_factor_batched(self.handle, self.ws, self.ws_bytes, self.info, stream)
+
+    def signature(self) -> str:
+        """Autotuner cache key: device, dtype, passes and the problem shapes."""
+        shapes = sorted((int(w.shape[0]), int(w.shape[1]), int(sk.k)) for sk, w in zip(self.sketches, self.W))
+        import hashlib
+
+        h = hashlib.sha1(repr(shapes).encode()).hexdigest()[:16]
+        return f"{torch.cuda.get_device_name(self.W[0].device)}|{self.W[0].dtype}|p{self.opts.passes}|{h}"
+
+    def tune(self, reps: int = 3, cache: str | None = None, stream=None) -> tuple:
+        """Pick the launch shapes: from the JSON cache when it holds this
+        signature, else by timing the candidates (and record them there)."""
+        key = self.signature()
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+            if key in table:
+                rhqr_batch_set_tuning(self.handle, table[key])
+                return tuple(table[key])
+        choice = rhqr_batch_tune(self.handle, self.ws, self.ws_bytes, self.info, reps, stream)
+        if cache:
+            table[key] = list(choice)
+            with open(cache, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+        return choice
+
+    def tuning(self) -> tuple:
+        return rhqr_batch_get_tuning(self.handle)
+
+    def capture(self):
+        """A CUDA graph that replays the whole batch (one graph launch)."""
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(device=self.W[0].device)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run(s)  # warm-up outside the capture
+        torch.cuda.current_stream().wait_stream(s)
+        with torch.cuda.graph(g, stream=s):
+            self.run(s)
+        return g
+
+    def infos(self) -> list[dict]:
+        rows = self.info.cpu().tolist()
+        return [dict(zip(("status", "column", "passes_done", "reserved"), r)) for r in rows]

@@ -3,6 +3,8 @@
 
 import ctypes
 
+import pytest
+
 import paper_2405_10923_gb300 as rh
 from paper_2405_10923_gb300 import build
 
@@ -36,3 +38,10 @@ def test_argument_errors_are_synchronous():
     assert rh.load().rhqr_sketch_create(100, 0, rh.SRHT, 0, 0, None, ctypes.byref(out)) == 1
     assert rh.load().rhqr_factor(None, None, 0, 10, 2, 10, None, None, 0, None, 0, None, None, None, 0, None, 0,
                                  None, None) == 1
+    # batch plans: empty batches and null handles are rejected on the host
+    assert rh.load().rhqr_batch_create(0, None, None, 0, None, None, None, None, None, None, None, None, None, None,
+                                       ctypes.byref(out)) == 1
+    assert rh.load().rhqr_factor_batched(None, None, 0, None, None) == 1
+    assert rh.load().rhqr_batch_destroy(None) == 0
+    with pytest.raises(rh.RHQRError):
+        rh.rhqr_batch_set_tuning(None, (512, 64, 0))
