@@ -71,7 +71,9 @@ typedef struct {
   int32_t want_Q;       /* write the thin Q (n x m, W's dtype); default 1          */
   int32_t scaling;      /* reflector scaling of Algorithm 2: 0 = <u_j, e_j> = 1
                            (default), 1 = ||s_j|| = sqrt 2                         */
-  int32_t reserved;
+  int32_t solve;        /* float32 Q = X R^{-1} of recRHQR (m <= 256): 0 = tensor-core
+                           product with the explicit inverse R^{-1} = D + E, Q = X D
+                           + X E (default), 1 = tensor-core row-wise substitution  */
   int64_t wait_budget;  /* spin iterations of a device-side wait before it gives up
                            with RHQR_ETIMEOUT (0 = library default)                */
 } rhqr_opts;

@@ -51,7 +51,7 @@ class rhqr_opts(ctypes.Structure):
         ("want_U", ctypes.c_int32),
         ("want_Q", ctypes.c_int32),
         ("scaling", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("solve", ctypes.c_int32),
         ("wait_budget", ctypes.c_int64),
     ]
 

@@ -14,6 +14,7 @@
 #include "sketch_tc.cuh"
 #include "small.cuh"
 #include "solve_tc.cuh"
+#include "solve_inv_tc.cuh"
 
 struct rhqr_sketch_s {
   rhqr::SketchView view;
@@ -273,6 +274,7 @@ struct RecBuffers {
   double *Z, *Spass, *Rpass, *Racc, *Rtmp, *beta, *SS, *StZ, *M, *Gm;
   char *TriT, *GT;
   float *TriT64;  // padded to a multiple of the tensor-core panel width
+  double *Rinv;   // R^{-1} of the pass (tensor-core product solve)
   int *err;
   char *hqr_ws;
   size_t hqr_bytes;
@@ -307,6 +309,7 @@ static rhqr_status carve_rec(Carver &c, const SketchView &v, int64_t n, int32_t 
   {
     int64_t mp64 = ceil_div(m, kSolvePanel) * kSolvePanel;
     b.TriT64 = c.take<float>((size_t)mp64 * mp64);
+    b.Rinv = c.take<double>((size_t)m * m);
     b.err = c.take<int>(4);
   }
   b.hqr_bytes = hqr_workspace_bytes(p, m);
@@ -325,14 +328,21 @@ static rhqr_status sketch_for_pass(const SketchView &v, int32_t m, const void *X
   return sketch_apply_simt(v, m, X, wt, n, m, ldx, Z, ldz, b.sk_ws, b.sk_bytes, st);
 }
 
-// Q = X Tri^{-1} over all n rows: tensor cores for float32 data (m <= 256),
-// the SIMT substitution otherwise.
+// Q = X Tri^{-1} over all n rows.  float32 data with m <= 256 runs on the
+// tensor cores: by default as the product with the explicit inverse (limb
+// products chosen for float32-level results), with opts.solve = 1 as the
+// row-wise substitution; other cases use the SIMT substitution.
 template <class T>
 static rhqr_status solve_rows(const T *X, int64_t ldx, int64_t n, int32_t m, const double *Tri, T *Q, int64_t ldq,
-                              RecBuffers &b, cudaStream_t st);
+                              RecBuffers &b, const rhqr_opts &o, rhqr_info *info, long long budget, cudaStream_t st);
 template <>
 rhqr_status solve_rows<float>(const float *X, int64_t ldx, int64_t n, int32_t m, const double *Tri, float *Q,
-                              int64_t ldq, RecBuffers &b, cudaStream_t st) {
+                              int64_t ldq, RecBuffers &b, const rhqr_opts &o, rhqr_info *info, long long budget,
+                              cudaStream_t st) {
+  if (o.solve == 0 && solve_inv_tc_supported(m) && (X != Q || ldx == ldq)) {
+    RHQR_TRY(upper_inverse(Tri, m, b.Rinv, st));
+    return rows_solve_inv_tc(X, ldx, n, m, b.Rinv, 0, Q, ldq, info, budget, st);
+  }
   if (solve_tc_supported(m)) {
     int32_t mp64 = (int32_t)(ceil_div(m, kSolvePanel) * kSolvePanel);
     RHQR_TRY(pad_transpose_to<float>(Tri, m, mp64, 1, b.TriT64, st));
@@ -343,7 +353,9 @@ rhqr_status solve_rows<float>(const float *X, int64_t ldx, int64_t n, int32_t m,
 }
 template <>
 rhqr_status solve_rows<double>(const double *X, int64_t ldx, int64_t n, int32_t m, const double *Tri, double *Q,
-                               int64_t ldq, RecBuffers &b, cudaStream_t st) {
+                               int64_t ldq, RecBuffers &b, const rhqr_opts &o, rhqr_info *info, long long budget,
+                               cudaStream_t st) {
+  (void)o, (void)info, (void)budget;
   RHQR_TRY(pad_transpose<double>(Tri, m, 1, (double *)b.TriT, st));
   return rows_solve<double>(X, ldx, 0, n, m, (const double *)b.TriT, Q, ldq, st);
 }
@@ -392,12 +404,12 @@ static rhqr_status rec_typed(const SketchView &v, const T *W, int32_t wt, int64_
         RHQR_TRY(top_from_s<T>(S, lds, m, U, ldu, st));
         if (Q != nullptr) RHQR_TRY(rows_form_q<T>(U, ldu, 0, m, m, (const T *)b.GT, Q, ldq, st));
       } else if (Q != nullptr) {
-        RHQR_TRY(solve_rows<T>(X, ldx, n, m, b.Rpass, Q, ldq, b, st));
+        RHQR_TRY(solve_rows<T>(X, ldx, n, m, b.Rpass, Q, ldq, b, o, info, budget, st));
       }
     } else {
       // Q_i = X_{i-1} R_i^{-1} becomes the next pass's input (in place in Q)
       PhaseScope ps(PH_SOLVE, st);
-      RHQR_TRY(solve_rows<T>(X, ldx, n, m, b.Rpass, Q, ldq, b, st));
+      RHQR_TRY(solve_rows<T>(X, ldx, n, m, b.Rpass, Q, ldq, b, o, info, budget, st));
       X = Q;
       ldx = ldq;
     }
@@ -439,7 +451,7 @@ rhqr_status rhqr_factor(rhqr_sketch s, const void *W, int32_t wt, int64_t n, int
   else rhqr_default_opts(&o);
   const int64_t p = (int64_t)s->view.k + m;
   if (ldw < n || lds < p) return RHQR_EINVAL;
-  if (o.scaling != 0 && o.scaling != 1) return RHQR_EINVAL;
+  if ((o.scaling != 0 && o.scaling != 1) || (o.solve != 0 && o.solve != 1)) return RHQR_EINVAL;
   if (o.alg != RHQR_ALG_LEFT && o.alg != RHQR_ALG_REC) return RHQR_EINVAL;
   if (o.want_Q && (Q == nullptr || ldq < n)) return RHQR_EINVAL;
   if ((o.want_U || o.alg == RHQR_ALG_LEFT) && (U == nullptr || ldu < n)) return RHQR_EINVAL;

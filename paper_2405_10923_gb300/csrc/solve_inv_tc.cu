@@ -1,0 +1,609 @@
+// Q = X Tri^{-1} for float32 X (n x m, m <= 256) on the tcgen05 tensor cores,
+// through the explicit inverse computed on the small side in float64:
+//   Tri^{-1} = D (I + F),  D = diag(Tri^{-1}),  F = D^{-1} E strictly upper,
+//   Y = A + A F  with  A = X D.
+// With Tri = R this forms recRHQR's Q = W R^{-1} (Section 3.3).  The loaders
+// scale X by D in float32 and split A into three bf16 limbs (float32 values
+// are sums of three bf16 numbers); the tensor cores accumulate A F (six limb
+// products of weight >= 2^-16, or three when F is small enough that the
+// dropped ones stay below float32 rounding) and then A itself, through an
+// exact identity block, last: until that step the float32 accumulator only
+// holds A F -- small next to Y in refinement passes, where Tri is close to a
+// signed identity -- so its per-instruction rounding acts at that scale.
+// With six products the big limb product and the rest go to two accumulators
+// that the epilogue adds in float32.
+//
+// Tiles of 128 rows.  Columns are grouped in chunks of 64; row chunk kc of F
+// feeds the column chunks c >= kc.  For m > 128 the column chunks are shared
+// between the two CTAs of a cluster, balanced by tensor-core work ({0, 3} and
+// {1, 2} for four chunks; {2} and {0, 1} for three); each CTA keeps its blocks
+// of F (three bf16 limbs) and a 64 x 64 identity in shared memory as B
+// operands.  Tensor memory per CTA: two A stages (one 64-column chunk, three
+// limbs x 32 columns) and two accumulators of up to 128 columns (a double
+// buffer, or the pair of the six-product case).  For an
+// in-place solve a CTA stores its columns of a tile only after the peer CTA's
+// loaders have read the tile (counters in its shared memory that the peer
+// increments).
+//
+// Warp roles: warp 0 issues the MMAs (one thread), warp 1 owns tensor memory,
+// warps 4-11 (two groups, one per A stage) load X, scale, split and store the
+// limbs to tensor memory (thread = row = tensor-memory lane), warps 12-15
+// drain the accumulator and store Y.  Every wait is bounded.
+#include <algorithm>
+
+#include "solve_inv_tc.cuh"
+#include "tcgen05.cuh"
+
+namespace rhqr {
+
+// ---- small side: R^{-1} ----------------------------------------------------
+// Column j of Rinv solves R x = e_j by a backward column sweep: once x_l is
+// known, the partial sums s_i (i < l) take R_il x_l; x_{l-1} then follows.
+// Lane q owns rows q, q + 32, ...; column l-1 of R is fetched while column l
+// is used.
+__global__ void upper_inverse_kernel(const double *R, int32_t m, double *Rinv) {
+  const int j = blockIdx.x, lane = threadIdx.x;
+  if (j >= m) return;
+  constexpr int PER = 8;  // rows per lane (m <= 256)
+  double s[PER], x[PER], rd[PER], cur[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = lane + 32 * q;
+    s[q] = 0.0;
+    x[q] = 0.0;
+    rd[q] = i <= j ? 1.0 / R[(int64_t)i * m + i] : 0.0;
+    cur[q] = i < j ? R[(int64_t)j * m + i] : 0.0;
+  }
+  double xl = 1.0 / R[(int64_t)j * m + j];
+  for (int l = j; l >= 1; --l) {
+    double nxt[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int i = lane + 32 * q;
+      nxt[q] = i < l - 1 ? R[(int64_t)(l - 1) * m + i] : 0.0;
+      if (i == l) x[q] = xl;
+      if (i < l) s[q] += cur[q] * xl;
+    }
+    double cand = 0.0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q)
+      if (lane + 32 * q == l - 1) cand = -s[q] * rd[q];
+    xl = __shfl_sync(0xffffffffu, cand, (l - 1) & 31);
+#pragma unroll
+    for (int q = 0; q < PER; ++q) cur[q] = nxt[q];
+  }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = lane + 32 * q;
+    if (i == 0) x[q] = xl;
+    if (i < m) Rinv[(int64_t)j * m + i] = i <= j ? x[q] : 0.0;
+  }
+}
+
+rhqr_status upper_inverse(const double *R, int32_t m, double *Rinv, cudaStream_t st) {
+  if (m < 1 || m > 256) return RHQR_ENOTSUP;
+  upper_inverse_kernel<<<m, 32, 0, st>>>(R, m, Rinv);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
+}
+
+namespace sit {
+
+constexpr int TILE = 128;
+constexpr int NUM_THREADS = 512;
+constexpr int LOAD_WARP0 = 4;  // two groups of four loader warps, one per A stage
+constexpr int EPI_WARP0 = 12;
+constexpr int A_COLS = 96;     // one A stage: 3 limbs x 32 columns (64 bf16 per lane)
+constexpr int ACC_COL0 = 2 * A_COLS;
+constexpr int MAX_W = 128;     // accumulator columns of one CTA (2 buffers + 2 A stages <= 512)
+constexpr int MAXM = 256;
+constexpr int MAXG = 8;        // MMA groups per CTA
+constexpr int ID_BYTES = 64 * 128;  // 64 x 64 bf16 identity, 128-byte swizzled
+constexpr int MAXPROG = 320;        // MMAs per tile of one CTA: groups x (6 x 4 + 12)
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+static_assert(NUM_THREADS == 512, "roles: warps 0-3 control, 4-11 loaders, 12-15 epilogue");
+
+// One MMA group: row chunk kc of F times the columns [c0, c0 + N) of this CTA.
+struct Grp {
+  int32_t kc, c0, N, acc;   // acc: accumulator column of c0
+  int32_t boff;             // byte offset of the three limb blocks (N rows x 128 bytes each)
+  int32_t id_acc, id_N;     // identity of column chunk kc afterwards (id_N = 0: none)
+};
+
+struct CtaPlan {
+  int32_t ngrp, nk;         // groups; row chunks to load (0 .. nk-1)
+  Grp g[MAXG];
+  int32_t ncc, cc[2], cc_acc[2], cc_w[2];  // owned column chunks: index, accumulator column, width
+  int32_t bbytes;
+};
+
+struct Params {
+  const float *X;
+  int64_t ldx;
+  float *Y;
+  int64_t ldy;
+  int64_t nrows;
+  int32_t m, nprod, split, bregion;  // nprod: 6, 3, or 0 = chosen from max |F|
+  const double *Rinv;
+  CtaPlan plan[2];
+  rhqr_info *info;
+  long long budget;
+};
+
+__device__ __forceinline__ void split3f(float x, __nv_bfloat16 &h, __nv_bfloat16 &mi, __nv_bfloat16 &lo) {
+  h = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(h);
+  mi = __float2bfloat16_rn(r1);
+  lo = __float2bfloat16_rn(r1 - __bfloat162float(mi));
+}
+__device__ __forceinline__ void split3d(double x, __nv_bfloat16 &h, __nv_bfloat16 &mi, __nv_bfloat16 &lo) {
+  h = __double2bfloat16(x);
+  const double r1 = x - (double)__bfloat162float(h);
+  mi = __double2bfloat16(r1);
+  lo = __double2bfloat16(r1 - (double)__bfloat162float(mi));
+}
+
+// Limb products of A F: the dropped ones (weight 2^-16) stay below float32
+// rounding of Y when 3 sqrt(m) max |F| <= 2^-8.
+__device__ __forceinline__ int choose_nprod(int forced, int m, float fmax) {
+  if (forced != 0) return forced;
+  return 3.f * sqrtf((float)m) * fmax <= 0.00390625f ? 3 : 6;
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1) solve_inv_tc_kernel(const __grid_constant__ Params P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *bsm = smem;                              // F blocks
+  uint8_t *idm = smem + P.bregion;                  // identity block
+  uint4 *prog = reinterpret_cast<uint4 *>(idm + ID_BYTES);  // the CTA's MMAs of one tile
+  float *dvec = reinterpret_cast<float *>(prog + MAXPROG);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(dvec + MAXM);
+  uint64_t *a_full = bars, *a_empty = bars + 2, *acc_full = bars + 4, *acc_empty = bars + 6;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 8);
+  volatile int *abort_s = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  int *err_s = reinterpret_cast<int *>(tmem_slot + 2);
+  unsigned int *fmax_s = tmem_slot + 3;  // max |F| of this CTA's blocks (float bits, >= 0)
+  uint32_t *peer_cnt = tmem_slot + 4;    // [2]: rows read by the peer's loader groups
+  uint32_t *pstart = tmem_slot + 8;      // [5]: first MMA of each row chunk in prog
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = P.split ? tc::cluster_ctarank() : 0u;
+  const CtaPlan &C = P.plan[rank];
+  const int m = P.m;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2; ++s) {
+      tc::mbar_init(a_full + s, 4);
+      tc::mbar_init(a_empty + s, 1);
+      tc::mbar_init(acc_full + s, 1);
+      tc::mbar_init(acc_empty + s, 4);
+    }
+    *abort_s = 0;
+    *err_s = 0;
+    *fmax_s = 0u;
+    peer_cnt[0] = 0;
+    peer_cnt[1] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // ---- B operands: F blocks (group g, limb l: N rows = columns c0 + n, 64 K
+  //      values = rows 64 kc .. 64 kc + 63), identity, and D
+  float fmax = 0.f;
+  for (int gi = 0; gi < C.ngrp; ++gi) {
+    const Grp &G = C.g[gi];
+    uint8_t *blk = bsm + G.boff;
+    for (int q = threadIdx.x; q < G.N * 8; q += NUM_THREADS) {
+      const int nrow = q >> 3, chunk = q & 7, j = G.c0 + nrow;
+      uint32_t w[3][4];
+#pragma unroll
+      for (int e2 = 0; e2 < 4; ++e2) {
+        double f[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int i = 64 * G.kc + chunk * 8 + 2 * e2 + h;
+          f[h] = (i < j && j < m) ? P.Rinv[(int64_t)j * m + i] / P.Rinv[(int64_t)i * m + i] : 0.0;
+          fmax = fmaxf(fmax, (float)fabs(f[h]));
+        }
+        __nv_bfloat16 ah, am, al, bh, bm, bl;
+        split3d(f[0], ah, am, al);
+        split3d(f[1], bh, bm, bl);
+        w[0][e2] = tc::pack_bf16(ah, bh);
+        w[1][e2] = tc::pack_bf16(am, bm);
+        w[2][e2] = tc::pack_bf16(al, bl);
+      }
+      const uint32_t off = tc::sw128_offset((uint32_t)nrow, (uint32_t)chunk);
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        *reinterpret_cast<uint4 *>(blk + (size_t)l * G.N * 128 + off) = make_uint4(w[l][0], w[l][1], w[l][2], w[l][3]);
+    }
+  }
+  for (int q = threadIdx.x; q < 64 * 8; q += NUM_THREADS) {
+    const int nrow = q >> 3, chunk = q & 7;
+    uint32_t w[4];
+    const __nv_bfloat16 one = __float2bfloat16_rn(1.f), zero = __float2bfloat16_rn(0.f);
+#pragma unroll
+    for (int e2 = 0; e2 < 4; ++e2) {
+      const int k0 = chunk * 8 + 2 * e2;
+      w[e2] = tc::pack_bf16(k0 == nrow ? one : zero, k0 + 1 == nrow ? one : zero);
+    }
+    *reinterpret_cast<uint4 *>(idm + tc::sw128_offset((uint32_t)nrow, (uint32_t)chunk)) =
+        make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  for (int j = threadIdx.x; j < MAXM; j += NUM_THREADS) dvec[j] = j < m ? (float)P.Rinv[(int64_t)j * m + j] : 0.f;
+  fmax = fmaxf(fmax, __shfl_xor_sync(0xffffffffu, fmax, 16));
+  fmax = fmaxf(fmax, __shfl_xor_sync(0xffffffffu, fmax, 8));
+  fmax = fmaxf(fmax, __shfl_xor_sync(0xffffffffu, fmax, 4));
+  fmax = fmaxf(fmax, __shfl_xor_sync(0xffffffffu, fmax, 2));
+  fmax = fmaxf(fmax, __shfl_xor_sync(0xffffffffu, fmax, 1));
+  if (lane == 0) atomicMax(fmax_s, __float_as_uint(fmax));
+  tc::fence_proxy_async();
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, 512);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (P.split) tc::cluster_sync();  // the peer's counters are initialised before anyone adds to them
+  const uint32_t tmem = *tmem_slot;
+
+  const int64_t ntiles = (P.nrows + TILE - 1) / TILE;
+  const int64_t t0 = P.split ? (int64_t)(blockIdx.x >> 1) : (int64_t)blockIdx.x;
+  const int64_t tstep = P.split ? (int64_t)(gridDim.x >> 1) : (int64_t)gridDim.x;
+
+  // Six products (F not small, e.g. the first pass of an ill-conditioned W):
+  // the big product A0 F0 and A0 through the identity go to one accumulator,
+  // the smaller products to a second one, summed in float32 by the epilogue,
+  // so that few tensor-core roundings act at the scale of the partial sums;
+  // one accumulator pair per CTA (the epilogue drains a tile before the next
+  // starts).  Three products: one accumulator, double-buffered.
+  const int nprod = choose_nprod(P.nprod, m, __uint_as_float(*fmax_s));
+  const bool two = nprod == 6;
+  const uint32_t nbuf = two ? 1u : 2u;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // The tile's MMAs as a table {accumulator column, A column, B descriptor
+      // (low word), instruction descriptor | accumulate << 31}, per row chunk.
+      {
+        const int pa6[6] = {2, 1, 0, 1, 0, 0}, pb6[6] = {0, 1, 2, 0, 1, 0};
+        const int pa3[3] = {1, 0, 0}, pb3[3] = {0, 1, 0};
+        const int *pa = two ? pa6 : pa3, *pb = two ? pb6 : pb3;
+        const uint32_t bsm_a = tc::smem_u32(bsm), id_a = tc::smem_u32(idm);
+        int e = 0, gi = 0;
+        for (int kc = 0; kc < C.nk; ++kc) {
+          pstart[kc] = (uint32_t)e;
+          for (; gi < C.ngrp && C.g[gi].kc == kc; ++gi) {
+            const Grp &G = C.g[gi];
+            const uint32_t idesc = tc::idesc_bf16(128, G.N);
+            // row-chunk-0 groups cover every owned column: their first MMA into
+            // each accumulator starts the sums
+            uint32_t on_s = G.kc > 0 ? 1u : 0u, on_b = on_s;
+            for (int pr = 0; pr < nprod; ++pr) {
+              const bool big = two && pr == nprod - 1;
+              uint32_t &on = big ? on_b : on_s;
+              const uint32_t blo = (uint32_t)tc::sw128_desc(bsm_a + (uint32_t)(G.boff + pb[pr] * G.N * 128));
+              for (int kk = 0; kk < 4; ++kk) {
+                prog[e++] = make_uint4((uint32_t)(G.acc + (big ? MAX_W : 0)), (uint32_t)(pa[pr] * 32 + kk * 8),
+                                       blo + (uint32_t)(2 * kk), idesc | (on << 31));
+                on = 1u;
+              }
+            }
+            if (G.id_N > 0) {  // + A through the identity: limbs smallest first
+              const uint32_t iid = tc::idesc_bf16(128, G.id_N);
+              const uint32_t blo = (uint32_t)tc::sw128_desc(id_a);
+              for (int l = 2; l >= 0; --l)
+                for (int kk = 0; kk < 4; ++kk)
+                  prog[e++] = make_uint4((uint32_t)(G.id_acc + (two && l == 0 ? MAX_W : 0)),
+                                         (uint32_t)(l * 32 + kk * 8), blo + (uint32_t)(2 * kk), iid | (1u << 31));
+            }
+          }
+        }
+        pstart[C.nk] = (uint32_t)e;
+      }
+      const uint32_t dhi = (uint32_t)(tc::sw128_desc(tc::smem_u32(bsm)) >> 32);
+      uint32_t gch = 0;
+      bool ok = true;
+      uint32_t it = 0;
+      for (int64_t t = t0; t < ntiles && ok; t += tstep, ++it) {
+        const uint32_t b = it % nbuf, u = it / nbuf;
+        if (!tc::mbar_wait(acc_empty + b, (u & 1u) ^ 1u, P.budget, err_s, abort_s)) break;
+        tc::fence_after();
+        const uint32_t acc = tmem + (uint32_t)(ACC_COL0 + b * MAX_W);
+        for (int kc = 0; kc < C.nk; ++kc, ++gch) {
+          const uint32_t s = gch & 1u;
+          if (!tc::mbar_wait(a_full + s, (gch >> 1) & 1u, P.budget, err_s, abort_s)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after();
+          const uint32_t a_stage = tmem + (uint32_t)(s * A_COLS);
+          const uint32_t e0 = pstart[kc], e1 = pstart[kc + 1];
+          uint4 E = prog[e0];
+          for (uint32_t e = e0; e < e1; ++e) {
+            const uint4 En = prog[e + 1 < e1 ? e + 1 : e];  // next entry, read ahead of the MMA
+            tc::mma_ts(acc + E.x, a_stage + E.y, ((uint64_t)dhi << 32) | E.z, E.w & 0x7fffffffu, E.w >> 31);
+            E = En;
+          }
+          tc::mma_commit(a_empty + s);
+        }
+        if (!ok) break;
+        tc::mma_commit(acc_full + b);
+      }
+    }
+    __syncwarp();
+  } else if (warp >= LOAD_WARP0 && warp < EPI_WARP0) {
+    // Loader group grp handles the chunks of even / odd global index, i.e. A
+    // stage grp; group 0 also prefetches the next tile of X into L2.
+    const int grp = (warp - LOAD_WARP0) >> 2;
+    const int qd = warp & 3;
+    const int r = qd * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
+    const uint32_t peer_addr = P.split ? tc::map_to_rank(peer_cnt + grp, rank ^ 1u) : 0u;
+    const int ncols = C.nk * 64 < m ? C.nk * 64 : m;
+    uint32_t gch = 0;
+    bool ok = true;
+    for (int64_t t = t0; t < ntiles && ok; t += tstep) {
+      const int64_t row = t * TILE + r;
+      const bool live = row < P.nrows;
+      if (grp == 0 && t + tstep < ntiles) {
+        // one 128-byte line per column and warp: lane l takes columns l, l + 32, ...
+        const int64_t r0 = (t + tstep) * TILE + qd * 32;
+        const int64_t rl = r0 + 31 < P.nrows ? r0 + 31 : P.nrows - 1;
+        if (r0 < P.nrows)
+          for (int col = lane; col < ncols; col += 32) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(P.X + (int64_t)col * P.ldx + r0));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(P.X + (int64_t)col * P.ldx + rl));
+          }
+      }
+      for (int kc = 0; kc < C.nk; ++kc, ++gch) {
+        if ((int)(gch & 1u) != grp) continue;
+        float v[64];
+#pragma unroll
+        for (int c = 0; c < 64; ++c) {
+          const int col = kc * 64 + c;
+          v[c] = (live && col < m) ? __ldg(P.X + (int64_t)col * P.ldx + row) : 0.f;
+        }
+        const uint32_t s = (uint32_t)grp, u = gch >> 1;
+        if (!tc::warp_wait(a_empty + s, (u & 1u) ^ 1u, P.budget, err_s, abort_s)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after();
+#pragma unroll
+        for (int pc = 0; pc < 4; ++pc) {
+          uint32_t w0[8], w1[8], w2[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int c = 16 * pc + 2 * j;
+            __nv_bfloat16 ah, am, al, bh, bm, bl;
+            split3f(v[c] * dvec[kc * 64 + c], ah, am, al);
+            split3f(v[c + 1] * dvec[kc * 64 + c + 1], bh, bm, bl);
+            w0[j] = tc::pack_bf16(ah, bh);
+            w1[j] = tc::pack_bf16(am, bm);
+            w2[j] = tc::pack_bf16(al, bl);
+          }
+          const uint32_t col = tmem + lane_base + (uint32_t)(s * A_COLS + pc * 8);
+          tc::tmem_st8(col, w0);
+          tc::tmem_st8(col + 32u, w1);
+          tc::tmem_st8(col + 64u, w2);
+        }
+        tc::tmem_wait_st();
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(a_full + s);
+      }
+      // this lane has read its row of the tile: tell the peer CTA
+      if (ok && P.split) tc::remote_add_release(peer_addr, 1u);
+    }
+  } else if (warp >= EPI_WARP0) {
+    const int qd = warp & 3;
+    const int r = qd * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
+    uint32_t it = 0;
+    for (int64_t t = t0; t < ntiles; t += tstep, ++it) {
+      const uint32_t b = it % nbuf, u = it / nbuf;
+      if (!tc::warp_wait(acc_full + b, u & 1u, P.budget, err_s, abort_s)) break;
+      tc::fence_after();
+      if (P.split) {  // in place: the peer's loaders must be done with this tile
+        const uint32_t need = 128u * (uint32_t)(it + 1);
+        long long spins = 0;
+        bool ok = true;
+        while (tc::ld_acquire_cluster(peer_cnt) < need || tc::ld_acquire_cluster(peer_cnt + 1) < need) {
+          if (*abort_s) {
+            ok = false;
+            break;
+          }
+          if (++spins > P.budget) {
+            atomicExch(err_s, 1);
+            *abort_s = 1;
+            ok = false;
+            break;
+          }
+        }
+        if (!__all_sync(0xffffffffu, ok)) break;
+      }
+      const int64_t row = t * TILE + r;
+      const bool live = row < P.nrows;
+      for (int ci = 0; ci < C.ncc; ++ci) {
+        for (int cb = 0; cb < C.cc_w[ci] / 16; ++cb) {
+          const uint32_t col = tmem + lane_base + (uint32_t)(ACC_COL0 + b * MAX_W + C.cc_acc[ci] + cb * 16);
+          uint32_t a[16], a2[16];
+          tc::tmem_ld16(col, a);
+          if (two) tc::tmem_ld16(col + (uint32_t)MAX_W, a2);
+          tc::tmem_wait_ld();
+          if (live) {
+            const int col0 = C.cc[ci] * 64 + cb * 16;
+            float *y = P.Y + (int64_t)col0 * P.ldy + row;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const float v = two ? __uint_as_float(a[j]) + __uint_as_float(a2[j]) : __uint_as_float(a[j]);
+              if (col0 + j < m) y[(int64_t)j * P.ldy] = v;
+            }
+          }
+        }
+      }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(acc_empty + b);
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after();
+    tc::tmem_dealloc(tmem, 512);
+  }
+  if (P.split) tc::cluster_sync();  // no peer adds into this CTA's shared memory after it exits
+  if (threadIdx.x == 0 && *err_s) set_status(P.info, RHQR_ETIMEOUT, -1);
+}
+
+// Plan of one CTA owning column chunks `own` (sorted) of mp columns.
+static bool make_plan(const int *own, int nown, int mp, CtaPlan &C) {
+  C = CtaPlan{};
+  int acc = 0;
+  for (int i = 0; i < nown; ++i) {
+    C.cc[i] = own[i];
+    C.cc_acc[i] = acc;
+    C.cc_w[i] = std::min(64, mp - 64 * own[i]);
+    acc += C.cc_w[i];
+  }
+  C.ncc = nown;
+  if (acc > MAX_W) return false;
+  C.nk = own[nown - 1] + 1;
+  int off = 0;
+  for (int kc = 0; kc < C.nk; ++kc) {
+    // owned chunks c >= kc, contiguous runs merged into one group
+    int i = 0;
+    while (i < nown) {
+      if (own[i] < kc) {
+        ++i;
+        continue;
+      }
+      int j = i;
+      while (j + 1 < nown && own[j + 1] == own[j] + 1) ++j;
+      if (C.ngrp >= MAXG) return false;
+      Grp &G = C.g[C.ngrp++];
+      G.kc = kc;
+      G.c0 = 64 * own[i];
+      G.acc = C.cc_acc[i];
+      G.N = 0;
+      for (int q = i; q <= j; ++q) G.N += C.cc_w[q];
+      G.boff = off;
+      off += 3 * G.N * 128;
+      G.id_N = 0;
+      G.id_acc = 0;
+      for (int q = i; q <= j; ++q)
+        if (own[q] == kc) {
+          G.id_N = C.cc_w[q];
+          G.id_acc = C.cc_acc[q];
+        }
+      i = j + 1;
+    }
+  }
+  C.bbytes = off;
+  return true;
+}
+
+static size_t smem_bytes(int bregion) {
+  return 1024 + (size_t)bregion + ID_BYTES + MAXPROG * 16 + MAXM * 4 + 8 * 8 + 64;
+}
+
+// Column chunks of the one or two CTAs per tile and the shared-memory size.
+static bool plan(int32_t m, Params &P, size_t *smem) {
+  if (m < 1 || m > MAXM) return false;
+  const int mp = (int)ceil_div(m, 16) * 16;
+  const int nc = (mp + 63) / 64;
+  bool ok;
+  if (nc <= 2) {
+    const int own[2] = {0, 1};
+    P.split = 0;
+    ok = make_plan(own, nc, mp, P.plan[0]);
+    P.plan[1] = P.plan[0];
+  } else if (nc == 3) {
+    const int a[1] = {2}, b[2] = {0, 1};
+    P.split = 1;
+    ok = make_plan(a, 1, mp, P.plan[0]) && make_plan(b, 2, mp, P.plan[1]);
+  } else {
+    const int a[2] = {0, 3}, b[2] = {1, 2};
+    P.split = 1;
+    ok = make_plan(a, 2, mp, P.plan[0]) && make_plan(b, 2, mp, P.plan[1]);
+  }
+  if (!ok) return false;
+  P.bregion = (int32_t)align_up((size_t)std::max(P.plan[0].bbytes, P.plan[1].bbytes), 1024);
+  *smem = smem_bytes(P.bregion);
+  return *smem <= SMEM_LIMIT;
+}
+
+}  // namespace sit
+
+bool solve_inv_tc_supported(int32_t m) {
+  sit::Params P;
+  size_t smem = 0;
+  return sit::plan(m, P, &smem);
+}
+
+rhqr_status rows_solve_inv_tc(const float *X, int64_t ldx, int64_t nrows, int32_t m, const double *Rinv, int nprod,
+                              float *Y, int64_t ldy, rhqr_info *info, long long budget, cudaStream_t st) {
+  if (nrows <= 0) return RHQR_OK;
+  if (nprod != 6 && nprod != 3 && nprod != 0) return RHQR_EINVAL;
+  if ((X == Y && ldx != ldy) || ldx < nrows || ldy < nrows) return RHQR_EINVAL;
+  sit::Params P;
+  size_t smem = 0;
+  if (!sit::plan(m, P, &smem)) return RHQR_ENOTSUP;
+  P.X = X;
+  P.ldx = ldx;
+  P.Y = Y;
+  P.ldy = ldy;
+  P.nrows = nrows;
+  P.m = m;
+  P.nprod = nprod;
+  P.Rinv = Rinv;
+  P.info = info;
+  P.budget = budget;
+  static bool attr_set = false;
+  static int sms = 0;
+  if (!attr_set) {
+    RHQR_CUDA_TRY(cudaFuncSetAttribute(sit::solve_inv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sit::SMEM_LIMIT));
+    int dev = 0;
+    RHQR_CUDA_TRY(cudaGetDevice(&dev));
+    RHQR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    attr_set = true;
+  }
+  const int64_t ntiles = ceil_div(nrows, sit::TILE);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(sit::NUM_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  if (P.split) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    static int max_clusters = 0;
+    if (max_clusters == 0) {
+      cfg.gridDim = dim3(2 * (unsigned)(sms / 2), 1, 1);
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, sit::solve_inv_tc_kernel, &cfg) != cudaSuccess || n < 1) {
+        (void)cudaGetLastError();
+        n = sms / 2;
+      }
+      max_clusters = n;
+    }
+    cfg.gridDim = dim3(2 * (unsigned)std::min<int64_t>(ntiles, max_clusters), 1, 1);
+  } else {
+    cfg.attrs = nullptr;
+    cfg.numAttrs = 0;
+    cfg.gridDim = dim3((unsigned)std::min<int64_t>(ntiles, sms), 1, 1);
+  }
+  RHQR_CUDA_TRY(cudaLaunchKernelEx(&cfg, sit::solve_inv_tc_kernel, P));
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
+}
+
+}  // namespace rhqr

@@ -58,10 +58,10 @@ class Sketch:
 
 
 def make_opts(alg=ALG_REC, passes=1, limbs_first=2, limbs_refine=2, want_U=False, want_Q=True, scaling=0,
-              wait_budget=0):
+              wait_budget=0, solve=0):
     o = rhqr_default_opts()
     o.alg, o.passes, o.limbs_first, o.limbs_refine = alg, passes, limbs_first, limbs_refine
-    o.want_U, o.want_Q, o.scaling, o.wait_budget = int(want_U), int(want_Q), scaling, wait_budget
+    o.want_U, o.want_Q, o.scaling, o.wait_budget, o.solve = int(want_U), int(want_Q), scaling, wait_budget, solve
     return o
 
 

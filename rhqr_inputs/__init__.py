@@ -114,6 +114,22 @@ def device_gaussian(n: int, m: int, seed: int, dtype=None, device="cuda"):
     return out
 
 
+def device_ragged_batch(count: int, n_lo: int, n_hi: int, m_choices, cond: float, seed: int, dtype=None,
+                        device="cuda"):
+    """The ragged batch workload on the device: n_i log-uniform in [n_lo, n_hi],
+    m_i uniform over m_choices; even i Gaussian, odd i log-spaced spectrum
+    1 .. 1/cond.  Returns (list of column-major W_i, n, m)."""
+    n, m = ragged_batch(count, n_lo, n_hi, m_choices, seed)
+    Ws = []
+    for i in range(count):
+        ni, mi = int(n[i]), int(m[i])
+        if i % 2 == 0:
+            Ws.append(device_gaussian(ni, mi, seed * 100003 + i, dtype, device))
+        else:
+            Ws.append(device_spectrum(ni, mi, cond, seed * 100003 + i, dtype, device))
+    return Ws, [int(x) for x in n], [int(x) for x in m]
+
+
 # ---------------------------------------------------------------------------
 # 2-D convection-diffusion operator (the GMRES workload), matrix-free
 # ---------------------------------------------------------------------------

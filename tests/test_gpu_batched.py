@@ -165,3 +165,32 @@ def test_batched_argument_errors(gpu_lib):
     b.close()
     sk.close()
     gk.close()
+
+
+def test_batched_full_size_sampled(gpu_lib):
+    """The full ragged workload (512 float32 problems, n_i log-uniform in
+    [16384, 262144], m_i in {16, 32, 64, 128}, k_i = 4 m_i, half Gaussian and
+    half cond 1e8 spectra, three passes) in the launch configuration the tuner
+    picks, replayed from a CUDA graph; sampled problems are checked with the
+    oracle's sketch, every problem's status and passes on the device."""
+    from paper_2405_10923_gb300 import torch_api as ta
+
+    Ws, ns, ms = ri.device_ragged_batch(512, 16384, 262144, (16, 32, 64, 128), 1e8, 4, torch.float32)
+    sks = [ta.Sketch(n, 4 * m, gpu_lib.SRHT, 7000 + i) for i, (n, m) in enumerate(zip(ns, ms))]
+    b = ta.Batch(sks, Ws, passes=3)
+    b.tune(reps=1)
+    g = b.capture()
+    for q in b.Q:
+        q.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    infos = b.infos()
+    assert all(x["status"] == 0 and x["passes_done"] == 3 for x in infos)
+    big = max(range(512), key=lambda i: ns[i] * ms[i])
+    for i in sorted({0, 1, 255, 510, 511, big}):
+        W = _np(Ws[i])
+        osk = sketch.SRHTSketch(ns[i], 4 * ms[i], 7000 + i)
+        Q = _np(b.Q[i])
+        assert metrics.sketch_orthogonality(Q, osk) <= 1e-5, i
+        assert metrics.residual(W, Q, _np(b.R[i])) <= 1e-5, i
+    b.close()

@@ -89,15 +89,20 @@ def test_mixed_rec_refined_meets_tolerance(gpu_lib, cond):
 # ---------------------------------------------------------------------------
 
 
+@pytest.mark.parametrize("solve", [0, 1])
 @pytest.mark.parametrize("n,m", [(5000, 256), (4099, 200), (3000, 130), (2000, 64), (2500, 65), (1000, 17),
-                                 (70001, 256)])
-def test_tc_solve_matches_oracle(gpu_lib, n, m):
+                                 (70001, 256), (300, 1), (127, 16), (20000, 161), (9000, 176), (6000, 255),
+                                 (1025, 160)])
+def test_tc_solve_matches_oracle(gpu_lib, n, m, solve):
+    """Both float32 tensor-core solves (explicit-inverse product, row-wise
+    substitution) over column counts that exercise one or two CTAs per row
+    tile, partial 16-column groups and row tiles smaller than 128."""
     from paper_2405_10923_gb300 import torch_api as ta
 
     k = max(2 * m, 64)
     W = ri.gaussian(n, m, 90).astype(np.float32).astype(np.float64)
     sk, osk = ta.Sketch(n, k, gpu_lib.SRHT, 91), sketch.SRHTSketch(n, k, 91)
-    out = ta.factor(sk, _dev(W), alg=gpu_lib.ALG_REC, passes=1)
+    out = ta.factor(sk, _dev(W), alg=gpu_lib.ALG_REC, passes=1, solve=solve)
     torch.cuda.synchronize()
     assert ta.info(out)["status"] == 0
     Q, R = _np(out["Q"]), _np(out["R"])
@@ -109,13 +114,14 @@ def test_tc_solve_matches_oracle(gpu_lib, n, m):
     sk.close()
 
 
-def test_tc_solve_in_place_refinement_high_condition(gpu_lib):
+@pytest.mark.parametrize("solve", [0, 1])
+def test_tc_solve_in_place_refinement_high_condition(gpu_lib, solve):
     from paper_2405_10923_gb300 import torch_api as ta
 
     n, m, k = 1 << 16, 256, 512
     W = ri.spectrum(n, m, 1e8, 92).astype(np.float32).astype(np.float64)
     sk, osk = ta.Sketch(n, k, gpu_lib.SRHT, 93), sketch.SRHTSketch(n, k, 93)
-    out = ta.factor(sk, _dev(W), alg=gpu_lib.ALG_REC, passes=3)
+    out = ta.factor(sk, _dev(W), alg=gpu_lib.ALG_REC, passes=3, solve=solve)
     torch.cuda.synchronize()
     assert ta.info(out)["passes_done"] == 3
     Q, R = _np(out["Q"]), _np(out["R"])
