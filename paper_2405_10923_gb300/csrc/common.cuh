@@ -138,6 +138,70 @@ __device__ __forceinline__ void set_status(rhqr_info *info, int32_t st, int32_t 
   if (atomicCAS(&info->status, (int)RHQR_OK, st) == RHQR_OK) info->column = col;
 }
 
+// Backward column sweep of an upper-triangular recurrence, one column per warp
+// (m <= 256; lane q owns rows q, q + 32, ...):
+//   x_j = top;  for l = j, ..., 1:  s_i += M[i, l] x_l (i < l),  x_{l-1} = f(l-1) s_{l-1}
+// with M column-major (M[i, l] at M[l * ldm + i]) and f(i) = -fin[i] (or, with
+// fin_recip_diag, -1 / M[i, i]).  Columns of M are fetched DEPTH steps ahead.
+// Writes x_i (i <= j) and 0 (j < i < m) to out[0 .. m).
+template <int DEPTH>
+__device__ __forceinline__ void column_sweep(const double *M, int64_t ldm, int32_t m, int j, double top,
+                                             const double *fin, bool fin_recip_diag, double *out) {
+  constexpr int PER = 8;
+  const int lane = threadIdx.x & 31;
+  double s[PER], x[PER], f[PER], buf[DEPTH][PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = lane + 32 * q;
+    s[q] = 0.0;
+    x[q] = 0.0;
+    f[q] = i < j ? (fin_recip_diag ? -1.0 / M[(int64_t)i * ldm + i] : -fin[i]) : 0.0;
+  }
+#pragma unroll
+  for (int d = 0; d < DEPTH; ++d)
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int l = j - d, i = lane + 32 * q;
+      buf[d][q] = (l >= 1 && i < l) ? M[(int64_t)l * ldm + i] : 0.0;
+    }
+  double xl = top;
+  int l = j;
+  while (l >= 1) {
+#pragma unroll
+    for (int d = 0; d < DEPTH; ++d) {
+      if (l >= 1) {
+        double cand = 0.0;
+        const int qa = (l + 31) >> 5;  // row groups with rows < l (warp-uniform)
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          if (q < qa) {
+            const int i = lane + 32 * q;
+            if (i == l) x[q] = xl;
+            if (i < l) s[q] += buf[d][q] * xl;
+            if (i == l - 1) cand = f[q] * s[q];
+          } else if (lane + 32 * q == l) {
+            x[q] = xl;
+          }
+        }
+        // refill this slot with column l - DEPTH
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          const int ln = l - DEPTH, i = lane + 32 * q;
+          buf[d][q] = (ln >= 1 && i < ln) ? M[(int64_t)ln * ldm + i] : 0.0;
+        }
+        xl = __shfl_sync(0xffffffffu, cand, (l - 1) & 31);
+        --l;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = lane + 32 * q;
+    if (i == 0) x[q] = xl;
+    if (i < m) out[i] = i <= j ? x[q] : 0.0;
+  }
+}
+
 // Grid-wide barrier for cooperative launches, with a bounded wait.
 // `bar[0]` counts arrivals, `bar[1]` is the generation.  Returns false (and
 // records RHQR_ETIMEOUT) if the wait ran out; every block then stops.

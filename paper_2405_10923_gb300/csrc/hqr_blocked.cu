@@ -1,0 +1,329 @@
+// Blocked Householder QR of the sketch Z (p x m, float64) for recRHQR
+// (Algorithm 6), same conventions as the column-by-column version in small.cu
+// (Algorithm 2 with Psi = I: sigma = sign(z_jj) with sign(0) = +1, rho =
+// ||z_{j:}||, v = z_{j:} / gamma with v_j = 1 or the ||v|| = sqrt 2 scaling,
+// beta = 1 + |z_jj| / rho, r_jj = -sigma rho).
+//
+// Panels of 32 columns.  A panel is factored by one cluster of CTAs that hold
+// its rows in shared memory; each column costs two cluster barriers, and the
+// partial sums of the CTAs are read from each other's shared memory and added
+// in rank order, so the result does not depend on timing.  The panel's
+// reflectors are then applied to the trailing columns in compact form,
+// Z_t <- (I - V T^t V^t) Z_t with T upper triangular (T_jj = beta_j,
+// T_{0:j,j} = -beta_j T_{0:j,0:j} V_{:,0:j}^t v_j), one CTA per trailing column.
+#include <algorithm>
+
+#include "common.cuh"
+#include "small.cuh"
+#include "tcgen05.cuh"
+
+namespace rhqr {
+namespace hb {
+
+__device__ __forceinline__ int64_t clamp64(int64_t v, int64_t lo, int64_t hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+constexpr int NB = 32;       // panel width
+constexpr int PT = 256;      // threads of a panel CTA
+constexpr int UT = 256;      // threads of an update CTA
+constexpr size_t SMEM_MAX = 200 * 1024;
+constexpr int MAXCS = 16;    // largest cluster
+
+struct Args {
+  double *A;  // p x m working copy, ld = p
+  int64_t p;
+  int32_t m, j0, nbp, per;  // panel [j0, j0 + nbp); rows per CTA of the panel cluster
+  double *S;
+  int64_t lds;
+  double *beta, *rdiag, *Tp;  // beta (m), -sigma rho (m), panel T (NB x NB, ld NB)
+  int *bad;                   // set once a breakdown / non-finite value is met
+  rhqr_info *info;
+  int32_t scaling;
+};
+
+__global__ void __launch_bounds__(PT) hqr_panel_kernel(Args a) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ double sh[4];
+  if (*(volatile int *)a.bad) return;  // identical for every CTA of the cluster
+  const uint32_t rank = tc::cluster_ctarank(), cs = gridDim.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = a.per, nbp = a.nbp, j0 = a.j0;
+  const int64_t p = a.p;
+  const int64_t row0 = (int64_t)j0 + (int64_t)rank * per;
+  const int nloc = (int)clamp64(p - row0, 0, per);
+  double *pan = sm;                      // [NB][per]: column c, local row i
+  double *part = sm + NB * per;          // [MAXCS][NB + 1]: partial sums pushed by every CTA
+  double *gram = part + MAXCS * (NB + 1);  // [NB][NB]: partial V^t V of this CTA
+  double *wsh = gram + NB * NB;          // [NB]
+  double *zsh = wsh + NB;                // [1]: z_jj pushed by its owner
+  for (int e = tid; e < nbp * per; e += PT) {
+    const int c = e / per, i = e % per;
+    pan[c * per + i] = i < nloc ? a.A[(int64_t)(j0 + c) * p + row0 + i] : 0.0;
+  }
+  __syncthreads();
+  for (int jc = 0; jc < nbp; ++jc) {
+    const int64_t j = (int64_t)j0 + jc;
+    const int lo = (int)clamp64(j - row0, 0, nloc);  // first own row >= j
+    // ---- ||z_{j:}||^2: one warp's partial sum over this CTA's rows, pushed
+    //      (with z_jj from its owner) into every CTA of the cluster, added there
+    //      in rank order.  FP64 instructions are scarce on this GPU: the scalar
+    //      work of the column is done once, by thread 0.
+    const uint32_t owner = (uint32_t)(jc / per);
+    if (warp == 0) {
+      double ss = 0.0;
+      for (int i = lo + lane; i < nloc; i += 32) ss += pan[jc * per + i] * pan[jc * per + i];
+      ss = warp_sum(ss);
+      if (lane < (int)cs) {
+        tc::st_cluster_f64(tc::map_to_rank(part + rank * (NB + 1), (uint32_t)lane), ss);
+        if (rank == owner) tc::st_cluster_f64(tc::map_to_rank(zsh, (uint32_t)lane), pan[jc * per + (jc - (int)owner * per)]);
+      }
+    }
+    tc::cluster_sync();
+    double tot = 0.0;
+    if (warp == 0) {
+      // partials of the CTAs added by a fixed lane tree (lane r holds rank r's)
+      tot = lane < (int)cs ? part[lane * (NB + 1)] : 0.0;
+      tot = warp_sum(tot);
+    }
+    if (tid == 0) {
+      const double rho = sqrt(tot), zjj = *zsh;
+      const bool fail = !isfinite(rho) || !isfinite(zjj) || rho == 0.0;
+      if (fail) {
+        if (rank == 0) {
+          set_status(a.info, rho == 0.0 ? RHQR_EBREAKDOWN : RHQR_ENONFINITE, (int32_t)j);
+          *a.bad = 1;
+        }
+      } else {
+        const double sigma = zjj < 0.0 ? -1.0 : 1.0;
+        const double gamma = zjj + sigma * rho;
+        if (a.scaling == 0) {  // v_j = 1, beta = 1 + |z_jj| / rho
+          sh[0] = 1.0 + fabs(zjj) / rho;
+          sh[1] = 1.0 / gamma;
+          sh[2] = 1.0;
+        } else {               // ||v|| = sqrt 2, beta = 1
+          const double rdiv = 1.0 / sqrt(rho * (rho + fabs(zjj)));
+          sh[0] = 1.0;
+          sh[1] = rdiv;
+          sh[2] = gamma * rdiv;
+        }
+        if (rank == 0) {
+          a.beta[j] = sh[0];
+          a.rdiag[j] = -sigma * rho;
+        }
+      }
+      sh[3] = fail ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (sh[3] != 0.0) {
+      tc::cluster_sync();  // no CTA leaves while another may still read its shared memory
+      return;
+    }
+    const double beta = sh[0], rdiv = sh[1], vjj = sh[2];
+    for (int i = lo + tid; i < nloc; i += PT) {
+      const int64_t gi = row0 + i;
+      pan[jc * per + i] = gi == j ? vjj : pan[jc * per + i] * rdiv;
+    }
+    __syncthreads();
+    // ---- v . z_c for the panel columns c > j, then z_c -= beta v (v . z_c)
+    for (int c = jc + 1 + warp; c < nbp; c += PT / 32) {
+      double d = 0.0;
+      for (int i = lo + lane; i < nloc; i += 32) d += pan[jc * per + i] * pan[c * per + i];
+      d = warp_sum(d);
+      if (lane < (int)cs) tc::st_cluster_f64(tc::map_to_rank(part + rank * (NB + 1) + 1 + c, (uint32_t)lane), d);
+    }
+    tc::cluster_sync();
+    // w_c = beta * (sum over ranks): half-warps add the 16 (or fewer) partials of a column by a lane tree
+    for (int c2 = jc + 1 + 2 * warp; c2 < nbp; c2 += 2 * (PT / 32)) {  // warp-uniform bound
+      const int c = c2 + (lane >> 4), r = lane & 15;
+      double w = (c < nbp && r < (int)cs) ? part[r * (NB + 1) + 1 + c] : 0.0;
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      if (r == 0 && c < nbp) wsh[c] = beta * w;
+    }
+    __syncthreads();
+    for (int e = tid; e < (nbp - jc - 1) * (nloc - lo); e += PT) {
+      const int c = jc + 1 + e / (nloc - lo), i = lo + e % (nloc - lo);
+      pan[c * per + i] -= pan[jc * per + i] * wsh[c];
+    }
+    __syncthreads();
+  }
+  // ---- the panel's T: partial V^t V (V[:, k] vanishes above row j0 + k)
+  for (int q = warp; q < nbp * nbp; q += PT / 32) {
+    const int k = q / nbp, l = q % nbp;
+    if (k >= l) continue;
+    const int lo = (int)clamp64((int64_t)j0 + l - row0, 0, nloc);
+    double d = 0.0;
+    for (int i = lo + lane; i < nloc; i += 32) d += pan[k * per + i] * pan[l * per + i];
+    d = warp_sum(d);
+    if (lane == 0) gram[k * NB + l] = d;
+  }
+  // write the factored panel back: A (v below the diagonal, R above), S
+  for (int e = tid; e < nbp * nloc; e += PT) {
+    const int c = e / nloc, i = e % nloc;
+    const int64_t gi = row0 + i, j = (int64_t)j0 + c;
+    const double v = pan[c * per + i];
+    a.A[j * p + gi] = v;
+    a.S[j * a.lds + gi] = gi < j ? 0.0 : v;
+  }
+  if (rank == 0)
+    for (int e = tid; e < nbp * j0; e += PT) a.S[(int64_t)(j0 + e / j0) * a.lds + e % j0] = 0.0;
+  tc::cluster_sync();
+  if (rank == 0 && warp == 0) {
+    // T column l = -beta_l T[0:l, 0:l] y, y_k = sum over CTAs of gram[k, l]; lane k owns row k
+    double *T = a.Tp;
+    for (int l = 0; l < nbp; ++l) {
+      double y = 0.0;
+      if (lane < l)
+        for (uint32_t r = 0; r < cs; ++r) y += tc::ld_cluster_f64(tc::map_to_rank(gram + lane * NB + l, r));
+      wsh[lane] = y;
+      __syncwarp();
+      double t = 0.0;
+      if (lane < l)
+        for (int q = lane; q < l; ++q) t += T[q * NB + lane] * wsh[q];
+      const double bl = a.beta[j0 + l];
+      __syncwarp();
+      if (lane < l) T[l * NB + lane] = -bl * t;
+      if (lane == l) T[l * NB + l] = bl;
+      if (lane > l) T[l * NB + lane] = 0.0;
+      __syncwarp();
+    }
+  }
+  tc::cluster_sync();  // peers finish reading this CTA's shared memory
+}
+
+// Z[:, c] <- Z[:, c] - V T^t V^t Z[:, c] for one trailing column c per CTA
+__global__ void __launch_bounds__(UT) hqr_update_kernel(Args a) {
+  __shared__ double w[NB], w2[NB];
+  if (*(volatile int *)a.bad) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t p = a.p, j0 = a.j0;
+  const int nbp = a.nbp;
+  double *z = a.A + (int64_t)(j0 + nbp + blockIdx.x) * p;
+  for (int k = warp; k < nbp; k += UT / 32) {
+    const double *v = a.S + (j0 + k) * a.lds;
+    double d = 0.0;
+    for (int64_t i = j0 + k + lane; i < p; i += 32) d += v[i] * z[i];
+    d = warp_sum(d);
+    if (lane == 0) w[k] = d;
+  }
+  __syncthreads();
+  if (tid < nbp) {
+    double t = 0.0;
+    for (int q = 0; q <= tid; ++q) t += a.Tp[tid * NB + q] * w[q];  // (T^t w)_tid
+    w2[tid] = t;
+  }
+  __syncthreads();
+  for (int64_t i = j0 + tid; i < p; i += UT) {
+    double acc = 0.0;
+    const int kmax = (int)clamp64(i - j0 + 1, 0, nbp);
+    for (int k = 0; k < kmax; ++k) acc += a.S[(j0 + k) * a.lds + i] * w2[k];
+    z[i] -= acc;
+  }
+}
+
+// R (m x m): the strict upper part from Z, the diagonal -sigma rho
+__global__ void hqr_r_kernel(const double *A, int64_t p, int32_t m, const double *rdiag, const int *bad, double *R) {
+  if (*bad) return;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)m * m) return;
+  const int j = (int)(idx / m), i = (int)(idx % m);
+  R[idx] = i < j ? A[(int64_t)j * p + i] : (i == j ? rdiag[j] : 0.0);
+}
+
+static size_t panel_smem(int per) {
+  return sizeof(double) * ((size_t)NB * per + (size_t)MAXCS * (NB + 1) + (size_t)NB * NB + NB + 2);
+}
+
+// Largest cluster (16, 8 or 4 CTAs) that fits the first panel of p rows.
+static int cluster_size(int64_t p) {
+  static int64_t cached_p = -1;
+  static int cached = 0;
+  if (cached_p == p) return cached;
+  int best = 0;
+  for (int cs : {16, 8, 4}) {
+    const size_t smem = panel_smem((int)ceil_div(p, cs));
+    if (smem > SMEM_MAX) continue;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(PT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, hqr_panel_kernel, &cfg) == cudaSuccess && n >= 1) {
+      best = cs;
+      break;
+    }
+    (void)cudaGetLastError();
+  }
+  cached_p = p;
+  cached = best;
+  return best;
+}
+
+}  // namespace hb
+
+size_t hqr_blocked_workspace_bytes(int64_t p, int32_t m) {
+  Carver c(nullptr, 0);
+  c.take<double>((size_t)p * m);
+  c.take<double>((size_t)m);
+  c.take<double>((size_t)hb::NB * hb::NB);
+  c.take<int>(4);
+  return c.used() + 256;
+}
+
+rhqr_status householder_qr_blocked(const double *Z, int64_t ldz, int64_t p, int32_t m, double *S, int64_t lds,
+                                   double *R, double *beta, int32_t scaling, void *ws, size_t ws_bytes,
+                                   rhqr_info *info, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    RHQR_CUDA_TRY(cudaFuncSetAttribute(hb::hqr_panel_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    RHQR_CUDA_TRY(
+        cudaFuncSetAttribute(hb::hqr_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hb::SMEM_MAX));
+    attr_set = true;
+  }
+  const int cs = hb::cluster_size(p);
+  if (cs == 0) return RHQR_ENOTSUP;
+  Carver c(ws, ws_bytes);
+  double *A = c.take<double>((size_t)p * m);
+  double *rdiag = c.take<double>((size_t)m);
+  double *Tp = c.take<double>((size_t)hb::NB * hb::NB);
+  int *bad = c.take<int>(4);
+  if (c.overflow()) return RHQR_ENOMEM;
+  RHQR_TRY(copy_f64_2d(Z, ldz, p, m, A, p, st));
+  RHQR_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  hb::Args a{A, p, m, 0, 0, 0, S, lds, beta, rdiag, Tp, bad, info, scaling};
+  for (int j0 = 0; j0 < m; j0 += hb::NB) {
+    a.j0 = j0;
+    a.nbp = std::min(hb::NB, m - j0);
+    a.per = (int)ceil_div(p - j0, cs);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(hb::PT, 1, 1);
+    cfg.dynamicSmemBytes = hb::panel_smem(a.per);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    RHQR_CUDA_TRY(cudaLaunchKernelEx(&cfg, hb::hqr_panel_kernel, a));
+    RHQR_LAUNCH_CHECK();
+    const int nt = m - j0 - a.nbp;
+    if (nt > 0) {
+      hb::hqr_update_kernel<<<nt, hb::UT, 0, st>>>(a);
+      RHQR_LAUNCH_CHECK();
+    }
+  }
+  hb::hqr_r_kernel<<<(unsigned)ceil_div((int64_t)m * m, 256), 256, 0, st>>>(A, p, m, rdiag, bad, R);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
+}
+
+}  // namespace rhqr

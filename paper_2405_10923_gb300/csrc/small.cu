@@ -11,6 +11,8 @@
 // T factor: Prop. "generalcompactwoodburry" gives (Psi U)^t Psi U = T^{-1} + T^{-t},
 //   i.e. T^{-1} = sut(S^t S) + diag(1/beta); T is obtained column by column by
 //   back substitution (columns are independent).
+// householder_qr_small uses the blocked version (hqr_blocked.cu) where its
+//   cluster fits.
 // Products of small triangular matrices (R accumulation over passes,
 //   G = T U_1^t, M = ut(T^t S^t Z)) and float32 copies for the row solves.
 #include "common.cuh"
@@ -120,22 +122,12 @@ __global__ void sts_upper_kernel(const double *S, int64_t lds, int64_t p, int32_
 }
 
 // T column j from T^{-1} = sut(S^t S) + diag(1/beta):
-//   T[j, j] = beta_j; T[i, j] = -beta_i sum_{l=i+1..j} SS[i, l] T[l, j], i = j-1..0
+//   T[j, j] = beta_j; T[i, j] = -beta_i sum_{l=i+1..j} SS[i, l] T[l, j], i = j-1..0,
+// as a backward column sweep over l (one warp per column).
 __global__ void t_from_woodbury_kernel(const double *SS, const double *beta, int32_t m, double *T) {
   const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
   if (j >= m) return;
-  double *t = T + (int64_t)j * m;
-  for (int i = j + 1 + lane; i < m; i += 32) t[i] = 0.0;
-  if (lane == 0) t[j] = beta[j];
-  __syncwarp();
-  for (int i = j - 1; i >= 0; --i) {
-    double d = 0.0;
-    for (int l = i + 1 + lane; l <= j; l += 32) d += SS[(int64_t)l * m + i] * t[l];
-    d = warp_sum(d);
-    if (lane == 0) t[i] = -beta[i] * d;
-    __syncwarp();
-  }
+  column_sweep<4>(SS, m, m, j, beta[j], beta, false, T + (int64_t)j * m);
 }
 
 // C = A B for upper-triangular m x m A, B (ld = m); C must not alias A or B.
@@ -226,12 +218,21 @@ size_t hqr_workspace_bytes(int64_t p, int32_t m) {
   c.take<double>((size_t)p * m);
   c.take<double>((size_t)128 * (m + 1));
   c.take<unsigned int>(4);
-  return c.used() + 256;
+  return std::max(c.used() + 256, hqr_blocked_workspace_bytes(p, m));
+}
+
+rhqr_status copy_f64_2d(const double *A, int64_t lda, int64_t p, int32_t m, double *B, int64_t ldb, cudaStream_t st) {
+  copy_f64_2d_kernel<<<(unsigned)ceil_div(p * m, 256), 256, 0, st>>>(A, lda, p, m, B, ldb);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
 }
 
 rhqr_status householder_qr_small(const double *Z, int64_t ldz, int64_t p, int32_t m, double *S, int64_t lds,
                                  double *R, double *beta, int32_t scaling, void *ws, size_t ws_bytes,
                                  rhqr_info *info, long long budget, cudaStream_t st) {
+  // blocked panels on clusters of CTAs where they fit, else column by column
+  const rhqr_status sb = householder_qr_blocked(Z, ldz, p, m, S, lds, R, beta, scaling, ws, ws_bytes, info, st);
+  if (sb != RHQR_ENOTSUP) return sb;
   Carver c(ws, ws_bytes);
   double *A = c.take<double>((size_t)p * m);
   double *part = c.take<double>((size_t)128 * (m + 1));

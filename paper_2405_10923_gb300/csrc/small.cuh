@@ -7,6 +7,13 @@
 namespace rhqr {
 
 size_t hqr_workspace_bytes(int64_t p, int32_t m);
+size_t hqr_blocked_workspace_bytes(int64_t p, int32_t m);
+
+// Blocked version (hqr_blocked.cu): RHQR_ENOTSUP when its cluster does not fit.
+rhqr_status householder_qr_blocked(const double *Z, int64_t ldz, int64_t p, int32_t m, double *S, int64_t lds,
+                                   double *R, double *beta, int32_t scaling, void *ws, size_t ws_bytes,
+                                   rhqr_info *info, cudaStream_t st);
+rhqr_status copy_f64_2d(const double *A, int64_t lda, int64_t p, int32_t m, double *B, int64_t ldb, cudaStream_t st);
 
 // Householder QR of Z (p x m, ldz): S (p x m, lds), R (m x m), beta (m).
 rhqr_status householder_qr_small(const double *Z, int64_t ldz, int64_t p, int32_t m, double *S, int64_t lds,

@@ -37,52 +37,18 @@
 namespace rhqr {
 
 // ---- small side: R^{-1} ----------------------------------------------------
-// Column j of Rinv solves R x = e_j by a backward column sweep: once x_l is
-// known, the partial sums s_i (i < l) take R_il x_l; x_{l-1} then follows.
-// Lane q owns rows q, q + 32, ...; column l-1 of R is fetched while column l
-// is used.
+// Column j of Rinv solves R x = e_j by a backward column sweep (one warp per
+// column): once x_l is known, the partial sums s_i (i < l) take R_il x_l and
+// x_{l-1} = -s_{l-1} / R_{l-1,l-1}.
 __global__ void upper_inverse_kernel(const double *R, int32_t m, double *Rinv) {
-  const int j = blockIdx.x, lane = threadIdx.x;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (j >= m) return;
-  constexpr int PER = 8;  // rows per lane (m <= 256)
-  double s[PER], x[PER], rd[PER], cur[PER];
-#pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int i = lane + 32 * q;
-    s[q] = 0.0;
-    x[q] = 0.0;
-    rd[q] = i <= j ? 1.0 / R[(int64_t)i * m + i] : 0.0;
-    cur[q] = i < j ? R[(int64_t)j * m + i] : 0.0;
-  }
-  double xl = 1.0 / R[(int64_t)j * m + j];
-  for (int l = j; l >= 1; --l) {
-    double nxt[PER];
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int i = lane + 32 * q;
-      nxt[q] = i < l - 1 ? R[(int64_t)(l - 1) * m + i] : 0.0;
-      if (i == l) x[q] = xl;
-      if (i < l) s[q] += cur[q] * xl;
-    }
-    double cand = 0.0;
-#pragma unroll
-    for (int q = 0; q < PER; ++q)
-      if (lane + 32 * q == l - 1) cand = -s[q] * rd[q];
-    xl = __shfl_sync(0xffffffffu, cand, (l - 1) & 31);
-#pragma unroll
-    for (int q = 0; q < PER; ++q) cur[q] = nxt[q];
-  }
-#pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int i = lane + 32 * q;
-    if (i == 0) x[q] = xl;
-    if (i < m) Rinv[(int64_t)j * m + i] = i <= j ? x[q] : 0.0;
-  }
+  column_sweep<4>(R, m, m, j, 1.0 / R[(int64_t)j * m + j], nullptr, true, Rinv + (int64_t)j * m);
 }
 
 rhqr_status upper_inverse(const double *R, int32_t m, double *Rinv, cudaStream_t st) {
   if (m < 1 || m > 256) return RHQR_ENOTSUP;
-  upper_inverse_kernel<<<m, 32, 0, st>>>(R, m, Rinv);
+  upper_inverse_kernel<<<(unsigned)ceil_div(m, 4), 128, 0, st>>>(R, m, Rinv);
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }

@@ -159,3 +159,17 @@ __device__ __forceinline__ uint32_t ld_acquire_cluster(const uint32_t *p) {
 
 }  // namespace tc
 }  // namespace rhqr
+
+namespace rhqr {
+namespace tc {
+// float64 load from shared memory of another CTA of the cluster (address from map_to_rank)
+__device__ __forceinline__ void st_cluster_f64(uint32_t cluster_addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(cluster_addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ double ld_cluster_f64(uint32_t cluster_addr) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(cluster_addr) : "memory");
+  return v;
+}
+}  // namespace tc
+}  // namespace rhqr
