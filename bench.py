@@ -36,9 +36,10 @@ UNIT = "GB/s"
 SAMPLE_ROWS = 16384  # rows of the bounded CPU sample (same m, k, recipe)
 REF_ROWS = 4096  # rows per step of the reference arm (about 4 s of CPU work each)
 
-# dram bytes per launch of each kernel from committed ncu captures
-# (profiles/*.md); None when the kernel changed since the counters were taken.
-TRAFFIC_BYTES = {"sketch": None, "solve": None, "hqr": None}
+# DRAM bytes (read + write) per launch at n = 2^22, m = 256, k = 1024, from ncu
+# captures at n = 2^20 scaled by 4 (both kernels stream W / Q and the operator in
+# proportion to n); None when the kernel changed since the counters were taken.
+TRAFFIC_BYTES = {"sketch": 4 * (3.760548e9 + 6.681344e6), "solve": 4 * (1.080e9 + 1.014e9), "hqr": None}
 
 
 def parse_args():
