@@ -169,10 +169,10 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes grouped in 8-row (1024-byte) atoms.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr, uint32_t sbo = 1024) {
   uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
   d |= (uint64_t)1 << 16;            // leading byte offset (unused with this swizzle)
-  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset: next 8-row atom
+  d |= (uint64_t)(sbo >> 4) << 32;   // stride byte offset: next 8-row atom
   d |= (uint64_t)1 << 46;            // descriptor version
   d |= (uint64_t)2 << 61;            // 128-byte swizzle
   return d;
@@ -206,13 +206,18 @@ struct Limb<__half> {
   }
 };
 
-template <class TL>
+template <class TL, int L>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     sketch_tc_kernel(const __grid_constant__ CUtensorMap tmapG, const __grid_constant__ CUtensorMap tmapX, Params P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int S = P.stages, L = P.limbs;
-  const int stage_bytes = A_BYTES + X_BYTES + L * B_BYTES;  // A | X staging | limbs
+  // With up to two limbs, X is split in place: the float32 staging of 8 columns
+  // (2 KiB) becomes their limb atoms (8 rows x 128 bytes each, 2 KiB apart per
+  // limb pair), so a stage is A | X and three stages fit; three limbs need a
+  // separate limb area (A | X staging | limbs, two stages).
+  constexpr bool INPLACE = L <= 2;
+  const int S = P.stages;
+  const int stage_bytes = INPLACE ? A_BYTES + X_BYTES : A_BYTES + X_BYTES + L * B_BYTES;
   uint64_t *bars = (uint64_t *)(smem + S * stage_bytes);
   uint64_t *full_a = bars, *full_b = bars + 4, *empty = bars + 8, *xempty = bars + 12;
   uint64_t *fresh_full = bars + 16, *fresh_empty = bars + 17;
@@ -257,7 +262,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int s = i % S;
         const uint32_t ph = (uint32_t)(i / S) & 1u;
         if (!mbar_wait(empty + s, ph ^ 1u, P.budget, P.err, abort_s) ||
-            !mbar_wait(xempty + s, ph ^ 1u, P.budget, P.err, abort_s)) {
+            (!INPLACE && !mbar_wait(xempty + s, ph ^ 1u, P.budget, P.err, abort_s))) {
           aborted = true;
           break;
         }
@@ -293,15 +298,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             break;
           }
           tc_fence_after();
+          // descriptors advance by (byte offset >> 4): the loops unroll to constant adds
           const uint32_t a_base = smem_u32(smem + s * stage_bytes);
-          const uint32_t b_base = a_base + A_BYTES + X_BYTES;
+          const uint64_t ad0 = sw128_desc(a_base);
+          const uint64_t bd0 = INPLACE ? sw128_desc(a_base + A_BYTES, 2048) : sw128_desc(a_base + A_BYTES + X_BYTES);
+          constexpr int LIMB_STRIDE = INPLACE ? 1024 : B_BYTES;
+#pragma unroll
           for (int h = 0; h < 2; ++h)
+#pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)
-              for (int l = 0; l < L; ++l) {
-                uint64_t ad = sw128_desc(a_base + h * (128 * 128) + kk * 32);
-                uint64_t bd = sw128_desc(b_base + l * B_BYTES + kk * 32);
-                mma_f16(tmem + (uint32_t)(h * NT), ad, bd, idesc, (uint32_t)((j | kk | l) != 0));
-              }
+#pragma unroll
+              for (int l = 0; l < L; ++l)
+                mma_f16(tmem + (uint32_t)(h * NT), ad0 + (uint64_t)((h * (128 * 128) + kk * 32) >> 4),
+                        bd0 + (uint64_t)((l * LIMB_STRIDE + kk * 32) >> 4), idesc,
+                        (uint32_t)(j != 0 || kk != 0 || l != 0));
           mma_commit(empty + s);
         }
         mma_commit(fresh_full);
@@ -318,8 +328,47 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint8_t *st = smem + s * stage_bytes;
       const float *xs = reinterpret_cast<const float *>(st + A_BYTES);
       uint8_t *bst = st + A_BYTES + X_BYTES;
+      uint8_t *bst_in = st + A_BYTES;
       const int64_t r0 = x_begin + (int64_t)i * BK;
       const bool top = r0 < P.m;  // rows below m are the exact top block: excluded
+      if (INPLACE) {
+        // one warp per group of 8 columns; lane = (column n, row quarter q)
+        const int n = lane >> 2, qr = lane & 3;
+        for (int g = warp - CONV_WARP0; g < P.Nt / 8; g += NUM_CONV_WARPS) {
+          const float4 *src = reinterpret_cast<const float4 *>(xs + (8 * g + n) * BK + 16 * qr);
+          float v[16];
+#pragma unroll
+          for (int e4 = 0; e4 < 4; ++e4) {
+            const float4 f = src[e4];
+            v[4 * e4] = f.x, v[4 * e4 + 1] = f.y, v[4 * e4 + 2] = f.z, v[4 * e4 + 3] = f.w;
+          }
+          if (top) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              if (r0 + 16 * qr + e < P.m) v[e] = 0.f;
+          }
+          __syncwarp();  // the whole group is read before its bytes are overwritten
+          uint8_t *atom = bst_in + g * 2048;
+#pragma unroll
+          for (int l = 0; l < L; ++l) {
+#pragma unroll
+            for (int h8 = 0; h8 < 2; ++h8) {  // rows 16 qr + 8 h8 .. + 7: one 16-byte chunk
+              uint4 w;
+              float r[8];
+              float *vv = v + 8 * h8;
+              w.x = Limb<TL>::pack(vv[0], vv[1], r[0], r[1]);
+              w.y = Limb<TL>::pack(vv[2], vv[3], r[2], r[3]);
+              w.z = Limb<TL>::pack(vv[4], vv[5], r[4], r[5]);
+              w.w = Limb<TL>::pack(vv[6], vv[7], r[6], r[7]);
+              const uint32_t chunk = (uint32_t)(2 * qr + h8);
+              *reinterpret_cast<uint4 *>(atom + l * 1024 + n * 128 + ((chunk ^ (uint32_t)(n & 7)) << 4)) = w;
+#pragma unroll
+              for (int e = 0; e < 8; ++e) vv[e] = r[e];
+            }
+          }
+          __syncwarp();
+        }
+      } else
       for (int q = ct; q < P.Nt * 8; q += NUM_CONV_WARPS * 32) {
         const int nn = q >> 3, cidx = q & 7;
         const float4 *src = reinterpret_cast<const float4 *>(xs + nn * BK + cidx * 8);
@@ -331,6 +380,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             if (r0 + cidx * 8 + e < P.m) v[e] = 0.f;
         }
         const uint32_t off = (uint32_t)nn * 128u + ((uint32_t)(cidx ^ (nn & 7)) << 4);
+#pragma unroll
         for (int l = 0; l < L; ++l) {
           uint4 w;
           float r[8];
@@ -402,6 +452,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_fence_after();
     tmem_dealloc(tmem, 512);
   }
+}
+
+template <class TL, int L>
+static rhqr_status launch_sketch(dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap &mapG,
+                                 const CUtensorMap &mapX, const Params &P) {
+  RHQR_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<TL, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sketch_tc_kernel<TL, L><<<grid, NUM_THREADS, smem, st>>>(mapG, mapX, P);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
 }
 
 // Z[ztop + r, c] = scale * sum_chunk part[chunk][c][r]  (float64, fixed order)
@@ -515,24 +574,28 @@ rhqr_status sketch_apply_tc(const SketchView &s, int32_t m, const float *X, int6
   P.k = s.k;
   P.kchunk = kchunk;
   P.limbs = limbs;
-  P.stages = 2;
+  P.stages = limbs <= 2 ? 3 : 2;
   P.kdrain = tc::KDRAIN;
   P.xbytes = tc::BK * Nt * 4;
   P.part = part;
   P.err = err;
   P.budget = 4000000LL;
-  size_t smem = 1024 + (size_t)P.stages * (tc::A_BYTES + tc::X_BYTES + (size_t)limbs * tc::B_BYTES) + 256;
+  const size_t stage_bytes = tc::A_BYTES + tc::X_BYTES + (limbs <= 2 ? 0 : (size_t)limbs * tc::B_BYTES);
+  size_t smem = 1024 + (size_t)P.stages * stage_bytes + 256;
   dim3 grid((unsigned)ceil_div(s.k, tc::BM), (unsigned)ceil_div(Np, Nt), (unsigned)nch);
   if (s.omega_dtype == RHQR_BF16) {
-    RHQR_CUDA_TRY(cudaFuncSetAttribute(tc::sketch_tc_kernel<__nv_bfloat16>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    tc::sketch_tc_kernel<__nv_bfloat16><<<grid, tc::NUM_THREADS, smem, st>>>(mapG, mapX, P);
+    switch (limbs) {
+      case 1: RHQR_TRY((tc::launch_sketch<__nv_bfloat16, 1>(grid, smem, st, mapG, mapX, P))); break;
+      case 2: RHQR_TRY((tc::launch_sketch<__nv_bfloat16, 2>(grid, smem, st, mapG, mapX, P))); break;
+      default: RHQR_TRY((tc::launch_sketch<__nv_bfloat16, 3>(grid, smem, st, mapG, mapX, P))); break;
+    }
   } else {
-    RHQR_CUDA_TRY(
-        cudaFuncSetAttribute(tc::sketch_tc_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    tc::sketch_tc_kernel<__half><<<grid, tc::NUM_THREADS, smem, st>>>(mapG, mapX, P);
+    switch (limbs) {
+      case 1: RHQR_TRY((tc::launch_sketch<__half, 1>(grid, smem, st, mapG, mapX, P))); break;
+      case 2: RHQR_TRY((tc::launch_sketch<__half, 2>(grid, smem, st, mapG, mapX, P))); break;
+      default: RHQR_TRY((tc::launch_sketch<__half, 3>(grid, smem, st, mapG, mapX, P))); break;
+    }
   }
-  RHQR_LAUNCH_CHECK();
   if (m > 0) {
     tc::copy_top_f32_kernel<<<(unsigned)ceil_div((int64_t)m * c, 256), 256, 0, st>>>(X, ldx, m, c, Z, ldz);
     RHQR_LAUNCH_CHECK();

@@ -1,38 +1,42 @@
 // Q = X Tri^{-1} for float32 X (n x m, m <= 256) on the tcgen05 tensor cores,
 // through the explicit inverse computed on the small side in float64:
 //   Tri^{-1} = D (I + F),  D = diag(Tri^{-1}),  F = D^{-1} E strictly upper,
-//   Y = A + A F  with  A = X D.
+//   Y = A (I + F)  with  A = X D.
 // With Tri = R this forms recRHQR's Q = W R^{-1} (Section 3.3).  The loaders
 // scale X by D in float32 and split A into three bf16 limbs (float32 values
-// are sums of three bf16 numbers); the tensor cores accumulate A F (six limb
-// products of weight >= 2^-16, or three when F is small enough that the
-// dropped ones stay below float32 rounding) and then A itself, through an
-// exact identity block, last: until that step the float32 accumulator only
-// holds A F -- small next to Y in refinement passes, where Tri is close to a
-// signed identity -- so its per-instruction rounding acts at that scale.
-// With six products the big limb product and the rest go to two accumulators
-// that the epilogue adds in float32.
+// are sums of three bf16 numbers); (I + F) is split into three bf16 limbs with
+// its unit diagonal exact.  For a column chunk, the products of the row chunk
+// that holds its diagonal come last and within them the big limb product
+// last, so the float32 accumulator only holds A F -- small next to Y in
+// refinement passes, where Tri is close to a signed identity -- until A itself
+// arrives.  Six limb products (weight >= 2^-16) are taken when F is not small,
+// with the big one in a second accumulator added in float32 by the epilogue;
+// three (plus A's smallest limb through the diagonal) when F is small enough
+// that the dropped ones stay below float32 rounding.
 //
-// Tiles of 128 rows.  Columns are grouped in chunks of 64; row chunk kc of F
-// feeds the column chunks c >= kc.  For m > 128 the column chunks are shared
-// between the two CTAs of a cluster, balanced by tensor-core work ({0, 3} and
-// {1, 2} for four chunks; {2} and {0, 1} for three); each CTA keeps its blocks
-// of F (three bf16 limbs) and a 64 x 64 identity in shared memory as B
+// Tiles of 128 rows.  Columns are grouped in chunks of 64; row chunk kc of
+// (I + F) feeds the column chunks c >= kc, one MMA group per row chunk.  For
+// m > 128 the column chunks are shared between the two CTAs of a cluster,
+// balanced by tensor work ({0, 3} and {1, 2} for four chunks; {2} and {0, 1}
+// for three); each CTA keeps its blocks of (I + F) in shared memory as B
 // operands.  Tensor memory per CTA: two A stages (one 64-column chunk, three
 // limbs x 32 columns) and two accumulators of up to 128 columns (a double
-// buffer, or the pair of the six-product case).  For an
-// in-place solve a CTA stores its columns of a tile only after the peer CTA's
-// loaders have read the tile (counters in its shared memory that the peer
-// increments).
+// buffer, or the pair of the six-product case).  For an in-place solve a CTA
+// stores its columns of a tile only after the peer CTA's loaders have read the
+// tile (counters in its shared memory that the peer increments).
 //
 // Warp roles: warp 0 issues the MMAs (one thread), warp 1 owns tensor memory,
-// warps 4-11 (two groups, one per A stage) load X, scale, split and store the
-// limbs to tensor memory (thread = row = tensor-memory lane), warps 12-15
-// drain the accumulator and store Y.  Every wait is bounded.
+// warp 2 loads X by TMA (64-column boxes of a tile, two stages) when X and its
+// leading dimension are 16-byte aligned, warps 4-11 (two groups, one per A
+// stage) scale, split and store the limbs to tensor memory (thread = row =
+// tensor-memory lane), warps 12-15 drain the accumulator and store Y.  Every
+// wait is bounded.
 #include <algorithm>
+#include <cstring>
 
 #include "solve_inv_tc.cuh"
 #include "tcgen05.cuh"
+#include "tma_host.cuh"
 
 namespace rhqr {
 
@@ -64,16 +68,17 @@ constexpr int ACC_COL0 = 2 * A_COLS;
 constexpr int MAX_W = 128;     // accumulator columns of one CTA (2 buffers + 2 A stages <= 512)
 constexpr int MAXM = 256;
 constexpr int MAXG = 8;        // MMA groups per CTA
-constexpr int ID_BYTES = 64 * 128;  // 64 x 64 bf16 identity, 128-byte swizzled
-constexpr int MAXPROG = 320;        // MMAs per tile of one CTA: groups x (6 x 4 + 12)
+constexpr int XST_BYTES = TILE * 64 * 4;  // one TMA stage of X: 128 rows x 64 columns float32
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 static_assert(NUM_THREADS == 512, "roles: warps 0-3 control, 4-11 loaders, 12-15 epilogue");
 
 // One MMA group: row chunk kc of F times the columns [c0, c0 + N) of this CTA.
+// Row chunk kc of (I + F) times the CTA's columns of chunks >= kc: they occupy
+// the accumulator columns [acc, acc + N) (owned chunks in order).
 struct Grp {
-  int32_t kc, c0, N, acc;   // acc: accumulator column of c0
-  int32_t boff;             // byte offset of the three limb blocks (N rows x 128 bytes each)
-  int32_t id_acc, id_N;     // identity of column chunk kc afterwards (id_N = 0: none)
+  int32_t kc, N, acc;  // acc: first accumulator column
+  int32_t boff;        // byte offset of the three limb blocks (N rows x 128 bytes each)
+  int32_t diag;        // chunk kc is owned: the block holds the identity's diagonal
 };
 
 struct CtaPlan {
@@ -90,6 +95,7 @@ struct Params {
   int64_t ldy;
   int64_t nrows;
   int32_t m, nprod, split, bregion;  // nprod: 6, 3, or 0 = chosen from max |F|
+  int32_t use_tma;                   // X staged by TMA (16-byte aligned X and ld), else column loads
   const double *Rinv;
   CtaPlan plan[2];
   rhqr_info *info;
@@ -116,21 +122,49 @@ __device__ __forceinline__ int choose_nprod(int forced, int m, float fmax) {
   return 3.f * sqrtf((float)m) * fmax <= 0.00390625f ? 3 : 6;
 }
 
-__global__ void __launch_bounds__(NUM_THREADS, 1) solve_inv_tc_kernel(const __grid_constant__ Params P) {
+// The MMAs of one group, smallest limb products first, fully unrolled:
+//   NPROD 3: (1,0) (0,1) (0,0)          [A limb, (I + F) limb]
+//   NPROD 4: (2,0) (1,0) (0,1) (0,0)    (the group holds a diagonal block: all
+//                                        three limbs of A pass through the identity)
+//   NPROD 6: (2,0) (1,1) (0,2) (1,0) (0,1) | (0,0) into the second accumulator
+template <int NPROD, bool TWO>
+__device__ __forceinline__ void issue_group(uint32_t dcol, uint32_t a_stage, uint32_t dhi, uint32_t blo,
+                                            uint32_t lstride, uint32_t idesc, bool first) {
+  constexpr int PA3[3] = {1, 0, 0}, PB3[3] = {0, 1, 0};
+  constexpr int PA4[4] = {2, 1, 0, 0}, PB4[4] = {0, 0, 1, 0};
+  constexpr int PA6[6] = {2, 1, 0, 1, 0, 0}, PB6[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+  for (int pr = 0; pr < NPROD; ++pr) {
+    const int pa = NPROD == 3 ? PA3[pr] : NPROD == 4 ? PA4[pr] : PA6[pr];
+    const int pb = NPROD == 3 ? PB3[pr] : NPROD == 4 ? PB4[pr] : PB6[pr];
+    const bool big = TWO && pr == NPROD - 1;
+    const uint32_t d = dcol + (big ? (uint32_t)MAX_W : 0u);
+    const uint32_t lo = blo + (uint32_t)pb * lstride;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      // the first MMA into an accumulator of row chunk 0 starts the sums
+      const uint32_t accumulate = (!first || kk > 0 || (pr > 0 && !big)) ? 1u : 0u;
+      tc::mma_ts(d, a_stage + (uint32_t)(pa * 32 + kk * 8), ((uint64_t)dhi << 32) | (lo + 2u * kk), idesc,
+                 accumulate);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    solve_inv_tc_kernel(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap tmapX) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t *bsm = smem;                              // F blocks
-  uint8_t *idm = smem + P.bregion;                  // identity block
-  uint4 *prog = reinterpret_cast<uint4 *>(idm + ID_BYTES);  // the CTA's MMAs of one tile
-  float *dvec = reinterpret_cast<float *>(prog + MAXPROG);
+  uint8_t *bsm = smem;                                         // (I + F) blocks
+  float *xst = reinterpret_cast<float *>(smem + P.bregion);    // 2 TMA stages [col][row]
+  float *dvec = xst + 2 * (XST_BYTES / 4);
   uint64_t *bars = reinterpret_cast<uint64_t *>(dvec + MAXM);
   uint64_t *a_full = bars, *a_empty = bars + 2, *acc_full = bars + 4, *acc_empty = bars + 6;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 8);
+  uint64_t *x_full = bars + 8, *x_empty = bars + 10;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 12);
   volatile int *abort_s = reinterpret_cast<volatile int *>(tmem_slot + 1);
   int *err_s = reinterpret_cast<int *>(tmem_slot + 2);
   unsigned int *fmax_s = tmem_slot + 3;  // max |F| of this CTA's blocks (float bits, >= 0)
   uint32_t *peer_cnt = tmem_slot + 4;    // [2]: rows read by the peer's loader groups
-  uint32_t *pstart = tmem_slot + 8;      // [5]: first MMA of each row chunk in prog
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = P.split ? tc::cluster_ctarank() : 0u;
@@ -143,6 +177,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_inv_tc_kernel(const __gr
       tc::mbar_init(a_empty + s, 1);
       tc::mbar_init(acc_full + s, 1);
       tc::mbar_init(acc_empty + s, 4);
+      tc::mbar_init(x_full + s, 1);
+      tc::mbar_init(x_empty + s, 4);
     }
     *abort_s = 0;
     *err_s = 0;
@@ -153,14 +189,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_inv_tc_kernel(const __gr
   }
   __syncthreads();
 
-  // ---- B operands: F blocks (group g, limb l: N rows = columns c0 + n, 64 K
-  //      values = rows 64 kc .. 64 kc + 63), identity, and D
+  // ---- B operands: (I + F) blocks (group g, limb l: N rows = the group's
+  //      columns j, 64 K values = rows 64 kc .. 64 kc + 63), and D.  Entry
+  //      (i, j): F_ij = Rinv_ij / Rinv_ii for i < j, 1 for i = j (exact in bf16).
   float fmax = 0.f;
   for (int gi = 0; gi < C.ngrp; ++gi) {
     const Grp &G = C.g[gi];
     uint8_t *blk = bsm + G.boff;
     for (int q = threadIdx.x; q < G.N * 8; q += NUM_THREADS) {
-      const int nrow = q >> 3, chunk = q & 7, j = G.c0 + nrow;
+      const int nrow = q >> 3, chunk = q & 7;
+      const int a = G.acc + nrow;  // accumulator column -> global column j
+      int ci = 0;
+      while (ci + 1 < C.ncc && a >= C.cc_acc[ci + 1]) ++ci;
+      const int j = 64 * C.cc[ci] + (a - C.cc_acc[ci]);
       uint32_t w[3][4];
 #pragma unroll
       for (int e2 = 0; e2 < 4; ++e2) {
@@ -168,8 +209,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_inv_tc_kernel(const __gr
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int i = 64 * G.kc + chunk * 8 + 2 * e2 + h;
-          f[h] = (i < j && j < m) ? P.Rinv[(int64_t)j * m + i] / P.Rinv[(int64_t)i * m + i] : 0.0;
-          fmax = fmaxf(fmax, (float)fabs(f[h]));
+          f[h] = 0.0;
+          if (j < m && i < j) {
+            f[h] = P.Rinv[(int64_t)j * m + i] / P.Rinv[(int64_t)i * m + i];
+            fmax = fmaxf(fmax, (float)fabs(f[h]));
+          } else if (j < m && i == j) {
+            f[h] = 1.0;
+          }
         }
         __nv_bfloat16 ah, am, al, bh, bm, bl;
         split3d(f[0], ah, am, al);
@@ -183,18 +229,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_inv_tc_kernel(const __gr
       for (int l = 0; l < 3; ++l)
         *reinterpret_cast<uint4 *>(blk + (size_t)l * G.N * 128 + off) = make_uint4(w[l][0], w[l][1], w[l][2], w[l][3]);
     }
-  }
-  for (int q = threadIdx.x; q < 64 * 8; q += NUM_THREADS) {
-    const int nrow = q >> 3, chunk = q & 7;
-    uint32_t w[4];
-    const __nv_bfloat16 one = __float2bfloat16_rn(1.f), zero = __float2bfloat16_rn(0.f);
-#pragma unroll
-    for (int e2 = 0; e2 < 4; ++e2) {
-      const int k0 = chunk * 8 + 2 * e2;
-      w[e2] = tc::pack_bf16(k0 == nrow ? one : zero, k0 + 1 == nrow ? one : zero);
-    }
-    *reinterpret_cast<uint4 *>(idm + tc::sw128_offset((uint32_t)nrow, (uint32_t)chunk)) =
-        make_uint4(w[0], w[1], w[2], w[3]);
   }
   for (int j = threadIdx.x; j < MAXM; j += NUM_THREADS) dvec[j] = j < m ? (float)P.Rinv[(int64_t)j * m + j] : 0.f;
   fmax = fmaxf(fmax, __shfl_xor_sync(0xffffffffu, fmax, 16));
@@ -230,45 +264,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_inv_tc_kernel(const __gr
 
   if (warp == 0) {
     if (lane == 0) {
-      // The tile's MMAs as a table {accumulator column, A column, B descriptor
-      // (low word), instruction descriptor | accumulate << 31}, per row chunk.
-      {
-        const int pa6[6] = {2, 1, 0, 1, 0, 0}, pb6[6] = {0, 1, 2, 0, 1, 0};
-        const int pa3[3] = {1, 0, 0}, pb3[3] = {0, 1, 0};
-        const int *pa = two ? pa6 : pa3, *pb = two ? pb6 : pb3;
-        const uint32_t bsm_a = tc::smem_u32(bsm), id_a = tc::smem_u32(idm);
-        int e = 0, gi = 0;
-        for (int kc = 0; kc < C.nk; ++kc) {
-          pstart[kc] = (uint32_t)e;
-          for (; gi < C.ngrp && C.g[gi].kc == kc; ++gi) {
-            const Grp &G = C.g[gi];
-            const uint32_t idesc = tc::idesc_bf16(128, G.N);
-            // row-chunk-0 groups cover every owned column: their first MMA into
-            // each accumulator starts the sums
-            uint32_t on_s = G.kc > 0 ? 1u : 0u, on_b = on_s;
-            for (int pr = 0; pr < nprod; ++pr) {
-              const bool big = two && pr == nprod - 1;
-              uint32_t &on = big ? on_b : on_s;
-              const uint32_t blo = (uint32_t)tc::sw128_desc(bsm_a + (uint32_t)(G.boff + pb[pr] * G.N * 128));
-              for (int kk = 0; kk < 4; ++kk) {
-                prog[e++] = make_uint4((uint32_t)(G.acc + (big ? MAX_W : 0)), (uint32_t)(pa[pr] * 32 + kk * 8),
-                                       blo + (uint32_t)(2 * kk), idesc | (on << 31));
-                on = 1u;
-              }
-            }
-            if (G.id_N > 0) {  // + A through the identity: limbs smallest first
-              const uint32_t iid = tc::idesc_bf16(128, G.id_N);
-              const uint32_t blo = (uint32_t)tc::sw128_desc(id_a);
-              for (int l = 2; l >= 0; --l)
-                for (int kk = 0; kk < 4; ++kk)
-                  prog[e++] = make_uint4((uint32_t)(G.id_acc + (two && l == 0 ? MAX_W : 0)),
-                                         (uint32_t)(l * 32 + kk * 8), blo + (uint32_t)(2 * kk), iid | (1u << 31));
-            }
-          }
-        }
-        pstart[C.nk] = (uint32_t)e;
-      }
       const uint32_t dhi = (uint32_t)(tc::sw128_desc(tc::smem_u32(bsm)) >> 32);
+      const uint32_t bsm_lo = (uint32_t)tc::sw128_desc(tc::smem_u32(bsm));
       uint32_t gch = 0;
       bool ok = true;
       uint32_t it = 0;
@@ -284,18 +281,45 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_inv_tc_kernel(const __gr
             break;
           }
           tc::fence_after();
+          const Grp &G = C.g[kc];  // one group per row chunk
           const uint32_t a_stage = tmem + (uint32_t)(s * A_COLS);
-          const uint32_t e0 = pstart[kc], e1 = pstart[kc + 1];
-          uint4 E = prog[e0];
-          for (uint32_t e = e0; e < e1; ++e) {
-            const uint4 En = prog[e + 1 < e1 ? e + 1 : e];  // next entry, read ahead of the MMA
-            tc::mma_ts(acc + E.x, a_stage + E.y, ((uint64_t)dhi << 32) | E.z, E.w & 0x7fffffffu, E.w >> 31);
-            E = En;
-          }
+          const uint32_t dcol = acc + (uint32_t)G.acc;
+          const uint32_t blo = bsm_lo + (uint32_t)(G.boff >> 4), lstride = (uint32_t)G.N * 8u;
+          const uint32_t idesc = tc::idesc_bf16(128, G.N);
+          const bool first = G.kc == 0;
+          if (two) issue_group<6, true>(dcol, a_stage, dhi, blo, lstride, idesc, first);
+          else if (G.diag) issue_group<4, false>(dcol, a_stage, dhi, blo, lstride, idesc, first);
+          else issue_group<3, false>(dcol, a_stage, dhi, blo, lstride, idesc, first);
           tc::mma_commit(a_empty + s);
         }
         if (!ok) break;
         tc::mma_commit(acc_full + b);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 2) {
+    if (lane == 0 && P.use_tma) {
+      // TMA producer: chunk G of the tile sequence goes to stage G & 1 (loader group G & 1)
+      uint32_t G = 0;
+      int last_u[2] = {-1, -1};  // use index of the last copy issued into each stage
+      bool ok = true;
+      for (int64_t t = t0; t < ntiles && ok; t += tstep)
+        for (int kc = 0; kc < C.nk; ++kc, ++G) {
+          const uint32_t s = G & 1u, u = G >> 1;
+          if (!tc::mbar_wait(x_empty + s, (u & 1u) ^ 1u, P.budget, err_s, abort_s)) {
+            ok = false;
+            break;
+          }
+          tc::mbar_expect_tx(x_full + s, (uint32_t)XST_BYTES);
+          tc::tma_load_2d(xst + s * (XST_BYTES / 4), &tmapX, x_full + s, (int)(t * TILE), kc * 64);
+          last_u[s] = (int)u;
+        }
+      if (!ok) {  // wait (bounded) for the copies still in flight before the CTA exits
+        for (int s = 0; s < 2; ++s) {
+          long long it = 0;
+          while (last_u[s] >= 0 && !tc::mbar_try_wait(x_full + s, (uint32_t)last_u[s] & 1u) && ++it < P.budget) {
+          }
+        }
       }
     }
     __syncwarp();
@@ -313,7 +337,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_inv_tc_kernel(const __gr
     for (int64_t t = t0; t < ntiles && ok; t += tstep) {
       const int64_t row = t * TILE + r;
       const bool live = row < P.nrows;
-      if (grp == 0 && t + tstep < ntiles) {
+      if (!P.use_tma && grp == 0 && t + tstep < ntiles) {
         // one 128-byte line per column and warp: lane l takes columns l, l + 32, ...
         const int64_t r0 = (t + tstep) * TILE + qd * 32;
         const int64_t rl = r0 + 31 < P.nrows ? r0 + 31 : P.nrows - 1;
@@ -326,12 +350,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_inv_tc_kernel(const __gr
       for (int kc = 0; kc < C.nk; ++kc, ++gch) {
         if ((int)(gch & 1u) != grp) continue;
         float v[64];
-#pragma unroll
-        for (int c = 0; c < 64; ++c) {
-          const int col = kc * 64 + c;
-          v[c] = (live && col < m) ? __ldg(P.X + (int64_t)col * P.ldx + row) : 0.f;
-        }
         const uint32_t s = (uint32_t)grp, u = gch >> 1;
+        if (P.use_tma) {
+          if (!tc::warp_wait(x_full + s, u & 1u, P.budget, err_s, abort_s)) {
+            ok = false;
+            break;
+          }
+          const float *xs = xst + s * (XST_BYTES / 4);
+#pragma unroll
+          for (int c = 0; c < 64; ++c) v[c] = xs[c * TILE + r];  // zero beyond the rows / columns of X
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(x_empty + s);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 64; ++c) {
+            const int col = kc * 64 + c;
+            v[c] = (live && col < m) ? __ldg(P.X + (int64_t)col * P.ldx + row) : 0.f;
+          }
+        }
         if (!tc::warp_wait(a_empty + s, (u & 1u) ^ 1u, P.budget, err_s, abort_s)) {
           ok = false;
           break;
@@ -438,43 +474,27 @@ static bool make_plan(const int *own, int nown, int mp, CtaPlan &C) {
   C.ncc = nown;
   if (acc > MAX_W) return false;
   C.nk = own[nown - 1] + 1;
+  if (C.nk > MAXG) return false;
   int off = 0;
   for (int kc = 0; kc < C.nk; ++kc) {
-    // owned chunks c >= kc, contiguous runs merged into one group
+    // the owned chunks c >= kc are a suffix of the owned list: one group
     int i = 0;
-    while (i < nown) {
-      if (own[i] < kc) {
-        ++i;
-        continue;
-      }
-      int j = i;
-      while (j + 1 < nown && own[j + 1] == own[j] + 1) ++j;
-      if (C.ngrp >= MAXG) return false;
-      Grp &G = C.g[C.ngrp++];
-      G.kc = kc;
-      G.c0 = 64 * own[i];
-      G.acc = C.cc_acc[i];
-      G.N = 0;
-      for (int q = i; q <= j; ++q) G.N += C.cc_w[q];
-      G.boff = off;
-      off += 3 * G.N * 128;
-      G.id_N = 0;
-      G.id_acc = 0;
-      for (int q = i; q <= j; ++q)
-        if (own[q] == kc) {
-          G.id_N = C.cc_w[q];
-          G.id_acc = C.cc_acc[q];
-        }
-      i = j + 1;
-    }
+    while (i < nown && own[i] < kc) ++i;
+    Grp &G = C.g[C.ngrp++];
+    G.kc = kc;
+    G.acc = C.cc_acc[i];
+    G.N = acc - C.cc_acc[i];
+    G.boff = off;
+    off += 3 * G.N * 128;
+    G.diag = 0;
+    for (int q = i; q < nown; ++q)
+      if (own[q] == kc) G.diag = 1;
   }
   C.bbytes = off;
   return true;
 }
 
-static size_t smem_bytes(int bregion) {
-  return 1024 + (size_t)bregion + ID_BYTES + MAXPROG * 16 + MAXM * 4 + 8 * 8 + 64;
-}
+static size_t smem_bytes(int bregion) { return 1024 + (size_t)bregion + 2 * XST_BYTES + MAXM * 4 + 12 * 8 + 64; }
 
 // Column chunks of the one or two CTAs per tile and the shared-memory size.
 static bool plan(int32_t m, Params &P, size_t *smem) {
@@ -528,6 +548,20 @@ rhqr_status rows_solve_inv_tc(const float *X, int64_t ldx, int64_t nrows, int32_
   P.Rinv = Rinv;
   P.info = info;
   P.budget = budget;
+  CUtensorMap mapX;
+  std::memset(&mapX, 0, sizeof(mapX));
+  P.use_tma = 0;
+  if ((ldx % 4) == 0 && ((uintptr_t)X % 16) == 0 && nrows < ((int64_t)1 << 31) - sit::TILE &&
+      tensor_map_encode_fn() != nullptr) {
+    cuuint64_t dims[2] = {(cuuint64_t)nrows, (cuuint64_t)m};
+    cuuint64_t strides[1] = {(cuuint64_t)ldx * 4};
+    cuuint32_t box[2] = {(cuuint32_t)sit::TILE, 64u};
+    cuuint32_t estr[2] = {1, 1};
+    if (tensor_map_encode_fn()(&mapX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), dims, strides, box,
+                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+      P.use_tma = 1;
+  }
   static bool attr_set = false;
   static int sms = 0;
   if (!attr_set) {
@@ -567,7 +601,7 @@ rhqr_status rows_solve_inv_tc(const float *X, int64_t ldx, int64_t nrows, int32_
     cfg.numAttrs = 0;
     cfg.gridDim = dim3((unsigned)std::min<int64_t>(ntiles, sms), 1, 1);
   }
-  RHQR_CUDA_TRY(cudaLaunchKernelEx(&cfg, sit::solve_inv_tc_kernel, P));
+  RHQR_CUDA_TRY(cudaLaunchKernelEx(&cfg, sit::solve_inv_tc_kernel, P, mapX));
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }
