@@ -189,20 +189,22 @@ template <>
 struct Limb<__nv_bfloat16> {
   static constexpr uint32_t fmt = 1;
   __device__ static __forceinline__ uint32_t pack(float a, float b, float &ra, float &rb) {
-    __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-    ra = a - __bfloat162float(ha);
-    rb = b - __bfloat162float(hb);
-    return (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // one packed conversion: a low, b high
+    const float2 hf = __bfloat1622float2(h);
+    ra = a - hf.x;
+    rb = b - hf.y;
+    return *reinterpret_cast<const uint32_t *>(&h);
   }
 };
 template <>
 struct Limb<__half> {
   static constexpr uint32_t fmt = 0;
   __device__ static __forceinline__ uint32_t pack(float a, float b, float &ra, float &rb) {
-    __half ha = __float2half_rn(a), hb = __float2half_rn(b);
-    ra = a - __half2float(ha);
-    rb = b - __half2float(hb);
-    return (uint32_t)__half_as_ushort(ha) | ((uint32_t)__half_as_ushort(hb) << 16);
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    ra = a - hf.x;
+    rb = b - hf.y;
+    return *reinterpret_cast<const uint32_t *>(&h);
   }
 };
 

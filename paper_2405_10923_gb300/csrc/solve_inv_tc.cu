@@ -29,8 +29,10 @@
 // warp 2 loads X by TMA (64-column boxes of a tile, two stages) when X and its
 // leading dimension are 16-byte aligned, warps 4-11 (two groups, one per A
 // stage) scale, split and store the limbs to tensor memory (thread = row =
-// tensor-memory lane), warps 12-15 drain the accumulator and store Y.  Every
-// wait is bounded.
+// tensor-memory lane), warps 12-15 drain the accumulator into shared memory
+// in pieces of 32 columns that one thread writes to Y with TMA stores (or,
+// when Y is not 16-byte aligned, store Y column by column).  Every wait is
+// bounded.
 #include <algorithm>
 #include <cstring>
 
@@ -69,6 +71,7 @@ constexpr int MAX_W = 128;     // accumulator columns of one CTA (2 buffers + 2 
 constexpr int MAXM = 256;
 constexpr int MAXG = 8;        // MMA groups per CTA
 constexpr int XST_BYTES = TILE * 64 * 4;  // one TMA stage of X: 128 rows x 64 columns float32
+constexpr int YST_BYTES = TILE * 32 * 4;  // one piece of Q for a TMA store: 128 rows x 32 columns
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 static_assert(NUM_THREADS == 512, "roles: warps 0-3 control, 4-11 loaders, 12-15 epilogue");
 
@@ -96,17 +99,24 @@ struct Params {
   int64_t nrows;
   int32_t m, nprod, split, bregion;  // nprod: 6, 3, or 0 = chosen from max |F|
   int32_t use_tma;                   // X staged by TMA (16-byte aligned X and ld), else column loads
+  int32_t use_tma_y;                 // Q written by TMA stores from shared memory, else column stores
   const double *Rinv;
   CtaPlan plan[2];
   rhqr_info *info;
   long long budget;
 };
 
-__device__ __forceinline__ void split3f(float x, __nv_bfloat16 &h, __nv_bfloat16 &mi, __nv_bfloat16 &lo) {
-  h = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(h);
-  mi = __float2bfloat16_rn(r1);
-  lo = __float2bfloat16_rn(r1 - __bfloat162float(mi));
+// three bf16 limbs of two float32 values at once (packed conversions; a low, b high)
+__device__ __forceinline__ void split3_pair(float a, float b, uint32_t &w0, uint32_t &w1, uint32_t &w2) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const float ra = a - hf.x, rb = b - hf.y;
+  const __nv_bfloat162 mi = __floats2bfloat162_rn(ra, rb);
+  const float2 mf = __bfloat1622float2(mi);
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(ra - mf.x, rb - mf.y);
+  w0 = *reinterpret_cast<const uint32_t *>(&h);
+  w1 = *reinterpret_cast<const uint32_t *>(&mi);
+  w2 = *reinterpret_cast<const uint32_t *>(&lo);
 }
 __device__ __forceinline__ void split3d(double x, __nv_bfloat16 &h, __nv_bfloat16 &mi, __nv_bfloat16 &lo) {
   h = __double2bfloat16(x);
@@ -151,12 +161,14 @@ __device__ __forceinline__ void issue_group(uint32_t dcol, uint32_t a_stage, uin
 }
 
 __global__ void __launch_bounds__(NUM_THREADS, 1)
-    solve_inv_tc_kernel(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap tmapX) {
+    solve_inv_tc_kernel(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap tmapX,
+                        const __grid_constant__ CUtensorMap tmapY32, const __grid_constant__ CUtensorMap tmapY16) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *bsm = smem;                                         // (I + F) blocks
   float *xst = reinterpret_cast<float *>(smem + P.bregion);    // 2 TMA stages [col][row]
-  float *dvec = xst + 2 * (XST_BYTES / 4);
+  float *ybuf = xst + 2 * (XST_BYTES / 4);                     // 2 pieces of Q [col][row]
+  float *dvec = ybuf + 2 * (YST_BYTES / 4);
   uint64_t *bars = reinterpret_cast<uint64_t *>(dvec + MAXM);
   uint64_t *a_full = bars, *a_empty = bars + 2, *acc_full = bars + 4, *acc_empty = bars + 6;
   uint64_t *x_full = bars + 8, *x_empty = bars + 10;
@@ -379,12 +391,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int c = 16 * pc + 2 * j;
-            __nv_bfloat16 ah, am, al, bh, bm, bl;
-            split3f(v[c] * dvec[kc * 64 + c], ah, am, al);
-            split3f(v[c + 1] * dvec[kc * 64 + c + 1], bh, bm, bl);
-            w0[j] = tc::pack_bf16(ah, bh);
-            w1[j] = tc::pack_bf16(am, bm);
-            w2[j] = tc::pack_bf16(al, bl);
+            split3_pair(v[c] * dvec[kc * 64 + c], v[c + 1] * dvec[kc * 64 + c + 1], w0[j], w1[j], w2[j]);
           }
           const uint32_t col = tmem + lane_base + (uint32_t)(s * A_COLS + pc * 8);
           tc::tmem_st8(col, w0);
@@ -403,10 +410,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int qd = warp & 3;
     const int r = qd * 32 + lane;
     const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
-    uint32_t it = 0;
+    uint32_t it = 0, piece = 0;
     for (int64_t t = t0; t < ntiles; t += tstep, ++it) {
       const uint32_t b = it % nbuf, u = it / nbuf;
-      if (!tc::warp_wait(acc_full + b, u & 1u, P.budget, err_s, abort_s)) break;
+      bool okw = tc::warp_wait(acc_full + b, u & 1u, P.budget, err_s, abort_s);
+      // the four epilogue warps share named barriers: they stop together
+      if (P.use_tma_y) okw = tc::named_and(1, 128, okw);
+      if (!okw) break;
       tc::fence_after();
       if (P.split) {  // in place: the peer's loaders must be done with this tile
         const uint32_t need = 128u * (uint32_t)(it + 1);
@@ -424,11 +434,43 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             break;
           }
         }
-        if (!__all_sync(0xffffffffu, ok)) break;
+        ok = __all_sync(0xffffffffu, ok);
+        if (P.use_tma_y) ok = tc::named_and(1, 128, ok);
+        if (!ok) break;
       }
       const int64_t row = t * TILE + r;
       const bool live = row < P.nrows;
+      const bool issuer = qd == 0 && lane == 0;  // the epilogue thread that issues TMA stores
       for (int ci = 0; ci < C.ncc; ++ci) {
+        if (P.use_tma_y) {
+          // pieces of 32 (or a last 16) columns: TMEM -> shared memory -> one TMA store
+          for (int c0 = 0; c0 < C.cc_w[ci]; c0 += 32, ++piece) {
+            const int wc = C.cc_w[ci] - c0 >= 32 ? 32 : 16;
+            float *yb = ybuf + (piece & 1u) * (YST_BYTES / 4);
+            if (issuer) tc::bulk_wait_read_1();  // the store that used this buffer has read it
+            tc::named_sync(1, 128);
+            for (int h = 0; h < wc / 16; ++h) {
+              const uint32_t col =
+                  tmem + lane_base + (uint32_t)(ACC_COL0 + b * MAX_W + C.cc_acc[ci] + c0 + 16 * h);
+              uint32_t a[16], a2[16];
+              tc::tmem_ld16(col, a);
+              if (two) tc::tmem_ld16(col + (uint32_t)MAX_W, a2);
+              tc::tmem_wait_ld();
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                yb[(16 * h + j) * TILE + r] =
+                    two ? __uint_as_float(a[j]) + __uint_as_float(a2[j]) : __uint_as_float(a[j]);
+            }
+            tc::fence_proxy_async();
+            tc::named_sync(1, 128);
+            if (issuer) {
+              tc::tma_store_2d(wc == 32 ? (const void *)&tmapY32 : (const void *)&tmapY16, yb, (int)(t * TILE),
+                               C.cc[ci] * 64 + c0);
+              tc::bulk_commit();
+            }
+          }
+          continue;
+        }
         for (int cb = 0; cb < C.cc_w[ci] / 16; ++cb) {
           const uint32_t col = tmem + lane_base + (uint32_t)(ACC_COL0 + b * MAX_W + C.cc_acc[ci] + cb * 16);
           uint32_t a[16], a2[16];
@@ -450,6 +492,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(acc_empty + b);
     }
+    if (P.use_tma_y && qd == 0 && lane == 0) tc::bulk_wait_all();  // stores complete before exit
   }
   tc::fence_before();
   __syncthreads();
@@ -494,7 +537,9 @@ static bool make_plan(const int *own, int nown, int mp, CtaPlan &C) {
   return true;
 }
 
-static size_t smem_bytes(int bregion) { return 1024 + (size_t)bregion + 2 * XST_BYTES + MAXM * 4 + 12 * 8 + 64; }
+static size_t smem_bytes(int bregion) {
+  return 1024 + (size_t)bregion + 2 * XST_BYTES + 2 * YST_BYTES + MAXM * 4 + 12 * 8 + 64;
+}
 
 // Column chunks of the one or two CTAs per tile and the shared-memory size.
 static bool plan(int32_t m, Params &P, size_t *smem) {
@@ -562,6 +607,24 @@ rhqr_status rows_solve_inv_tc(const float *X, int64_t ldx, int64_t nrows, int32_
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
       P.use_tma = 1;
   }
+  CUtensorMap mapY32, mapY16;
+  std::memset(&mapY32, 0, sizeof(mapY32));
+  std::memset(&mapY16, 0, sizeof(mapY16));
+  P.use_tma_y = 0;
+  if (P.use_tma && (ldy % 4) == 0 && ((uintptr_t)Y % 16) == 0) {
+    cuuint64_t dims[2] = {(cuuint64_t)nrows, (cuuint64_t)m};
+    cuuint64_t strides[1] = {(cuuint64_t)ldy * 4};
+    cuuint32_t estr[2] = {1, 1};
+    cuuint32_t box32[2] = {(cuuint32_t)sit::TILE, 32u}, box16[2] = {(cuuint32_t)sit::TILE, 16u};
+    auto enc = tensor_map_encode_fn();
+    if (enc(&mapY32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, Y, dims, strides, box32, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
+        enc(&mapY16, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, Y, dims, strides, box16, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+            CUDA_SUCCESS)
+      P.use_tma_y = 1;
+  }
   static bool attr_set = false;
   static int sms = 0;
   if (!attr_set) {
@@ -601,7 +664,7 @@ rhqr_status rows_solve_inv_tc(const float *X, int64_t ldx, int64_t nrows, int32_
     cfg.numAttrs = 0;
     cfg.gridDim = dim3((unsigned)std::min<int64_t>(ntiles, sms), 1, 1);
   }
-  RHQR_CUDA_TRY(cudaLaunchKernelEx(&cfg, sit::solve_inv_tc_kernel, P, mapX));
+  RHQR_CUDA_TRY(cudaLaunchKernelEx(&cfg, sit::solve_inv_tc_kernel, P, mapX, mapY32, mapY16));
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }
