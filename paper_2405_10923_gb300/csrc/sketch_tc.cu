@@ -17,7 +17,7 @@
 //   warp 0       : TMA producer: G tile (256 x 64 bf16, 128-byte swizzle) and
 //                  X tile (64 rows x Nt float32) per stage
 //   warp 1       : tensor-memory allocation and the single MMA-issuing thread
-//   warps 4..7   : converters: staged X -> L limbs in the K-major 128-byte
+//   warps 2..7   : converters: staged X -> L limbs in the K-major 128-byte
 //                  swizzled layout the MMA reads (rows < m are zeroed)
 //   warps 8..15  : drainers: fresh accumulator + running sum -> running sum;
 //                  at the end the running sums go to a float32 partial
@@ -38,7 +38,7 @@ constexpr int BK = 64;   // rows of X per stage (128 bytes of a 16-bit limb)
 constexpr int NT = 128;  // max columns of X per CTA
 constexpr int MAXC = 256;
 constexpr int NUM_THREADS = 512;
-constexpr int CONV_WARP0 = 4, NUM_CONV_WARPS = 4;
+constexpr int CONV_WARP0 = 2, NUM_CONV_WARPS = 6;
 constexpr int DRAIN_WARP0 = 8, NUM_DRAIN_WARPS = 8;
 constexpr int A_BYTES = BM * BK * 2;    // 32 KiB
 constexpr int B_BYTES = NT * BK * 2;    // 16 KiB per limb
@@ -334,38 +334,43 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int64_t r0 = x_begin + (int64_t)i * BK;
       const bool top = r0 < P.m;  // rows below m are the exact top block: excluded
       if (INPLACE) {
-        // one warp per group of 8 columns; lane = (column n, row quarter q)
-        const int n = lane >> 2, qr = lane & 3;
+        // One warp per group of 8 columns (2 KiB of float32, 64 rows each).  Load
+        // e4 of lane l is float4 f = 32 e4 + l: column f / 16, rows 4 (f % 16) ..
+        // + 3, so each 8-lane phase reads 128 contiguous bytes (no bank
+        // conflicts); the lane then writes its 4 rows of each limb as 8 bytes of
+        // the swizzled atom row of that column.
         for (int g = warp - CONV_WARP0; g < P.Nt / 8; g += NUM_CONV_WARPS) {
-          const float4 *src = reinterpret_cast<const float4 *>(xs + (8 * g + n) * BK + 16 * qr);
+          const float4 *src = reinterpret_cast<const float4 *>(xs + 8 * g * BK);
           float v[16];
 #pragma unroll
           for (int e4 = 0; e4 < 4; ++e4) {
-            const float4 f = src[e4];
+            const float4 f = src[32 * e4 + lane];
             v[4 * e4] = f.x, v[4 * e4 + 1] = f.y, v[4 * e4 + 2] = f.z, v[4 * e4 + 3] = f.w;
           }
           if (top) {
 #pragma unroll
-            for (int e = 0; e < 16; ++e)
-              if (r0 + 16 * qr + e < P.m) v[e] = 0.f;
+            for (int e4 = 0; e4 < 4; ++e4)
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                if (r0 + 4 * ((32 * e4 + lane) & 15) + e < P.m) v[4 * e4 + e] = 0.f;
           }
           __syncwarp();  // the whole group is read before its bytes are overwritten
           uint8_t *atom = bst_in + g * 2048;
 #pragma unroll
-          for (int l = 0; l < L; ++l) {
+          for (int e4 = 0; e4 < 4; ++e4) {
+            const int f = 32 * e4 + lane, n = f >> 4, row = 4 * (f & 15);
+            const uint32_t off = (uint32_t)n * 128u + ((((uint32_t)row >> 3) ^ (uint32_t)(n & 7)) << 4) +
+                                 (uint32_t)((row & 7) * 2);
+            float *vv = v + 4 * e4;
 #pragma unroll
-            for (int h8 = 0; h8 < 2; ++h8) {  // rows 16 qr + 8 h8 .. + 7: one 16-byte chunk
-              uint4 w;
-              float r[8];
-              float *vv = v + 8 * h8;
-              w.x = Limb<TL>::pack(vv[0], vv[1], r[0], r[1]);
-              w.y = Limb<TL>::pack(vv[2], vv[3], r[2], r[3]);
-              w.z = Limb<TL>::pack(vv[4], vv[5], r[4], r[5]);
-              w.w = Limb<TL>::pack(vv[6], vv[7], r[6], r[7]);
-              const uint32_t chunk = (uint32_t)(2 * qr + h8);
-              *reinterpret_cast<uint4 *>(atom + l * 1024 + n * 128 + ((chunk ^ (uint32_t)(n & 7)) << 4)) = w;
+            for (int l = 0; l < L; ++l) {
+              float rr[4];
+              uint2 w;
+              w.x = Limb<TL>::pack(vv[0], vv[1], rr[0], rr[1]);
+              w.y = Limb<TL>::pack(vv[2], vv[3], rr[2], rr[3]);
+              *reinterpret_cast<uint2 *>(atom + l * 1024 + off) = w;
 #pragma unroll
-              for (int e = 0; e < 8; ++e) vv[e] = r[e];
+              for (int e = 0; e < 4; ++e) vv[e] = rr[e];
             }
           }
           __syncwarp();
