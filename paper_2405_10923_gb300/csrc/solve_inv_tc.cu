@@ -371,6 +371,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const float *xs = xst + s * (XST_BYTES / 4);
 #pragma unroll
           for (int c = 0; c < 64; ++c) v[c] = xs[c * TILE + r];  // zero beyond the rows / columns of X
+          // the stage is refilled by TMA (async proxy) after this release: the fence
+          // completes these shared-memory reads before any lane signals it
+          tc::fence_proxy_async();
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(x_empty + s);
         } else {

@@ -128,3 +128,25 @@ def test_tc_solve_in_place_refinement_high_condition(gpu_lib, solve):
     assert metrics.residual(W, Q, R) <= 1e-5
     assert metrics.sketch_orthogonality(Q, osk) <= 1e-5
     sk.close()
+
+
+def test_tc_factor_repeatable_bitwise(gpu_lib):
+    """Every kernel of the float32 path is deterministic (fixed-order reductions,
+    no atomics on data): repeated factorisations of the same W give the same
+    bits.  A stage of a TMA pipeline released before its shared-memory reads had
+    completed once let a refill overwrite a tile's data; this repeats the
+    factorisation enough times to catch such a race."""
+    from paper_2405_10923_gb300 import torch_api as ta
+
+    n, m, k = 1 << 21, 256, 1024
+    W = ri.device_spectrum(n, m, 1e10, 94)
+    sk = ta.Sketch(n, k, gpu_lib.GAUSSIAN, 95, gpu_lib.BF16)
+    out = ta.factor(sk, W, alg=gpu_lib.ALG_REC, passes=3)
+    ws = out["ws"]
+    torch.cuda.synchronize()
+    Q0, R0 = out["Q"].clone(), out["R"].clone()
+    for _ in range(12):
+        ta.factor(sk, W, alg=gpu_lib.ALG_REC, passes=3, out=out, ws=ws)
+        torch.cuda.synchronize()
+        assert torch.equal(out["Q"], Q0) and torch.equal(out["R"], R0)
+    sk.close()
