@@ -1,0 +1,135 @@
+"""Timing of the library on the paper-shaped workloads other than the main
+benchmark (one JSON line per case, CUDA-event times of whole calls after
+warm-up, inputs resident on the device):
+
+  left_small  : left-looking RHQR (Algorithm 4), W 4096 x 32 float64 Gaussian,
+                Gaussian sketch k = 128, float64 -- latency per factorisation
+  srht_left   : left-looking RHQR, W = A diag(sigma) B 2^20 x 128 (sigma 1 ..
+                1e-12), SRHT k = 512, float64 and float32
+  srht_rec    : recRHQR + refinement on the same matrix and sketch, float64
+                (2 passes) and float32 (3 passes)
+  arnoldi     : RHQR-Arnoldi steps (Algorithm 7) with the 2-D convection-
+                diffusion operator on a 1024 x 1024 grid (n = 2^20, Peclet 10),
+                SRHT k = 400, 100 steps, float64 and float32 basis; the operator
+                (torch, matrix-free) is timed with the step, as a user runs it
+
+python -m paper_2405_10923_gb300.workloads_case [--cases left_small srht_left srht_rec arnoldi] [--reps 3]
+
+Accuracy is reported with the library's own sketch of the result in float64
+(orth = max |eig(I - (Psi Q)^t Psi Q)|) and resid = ||W - QR||_F / ||W||_F
+computed with torch."""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def _time(fn, reps):
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--cases", nargs="+", default=["left_small", "srht_left", "srht_rec", "arnoldi"])
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args()
+
+    import numpy as np
+    import torch
+
+    import paper_2405_10923_gb300 as rh
+    import rhqr_inputs as ri
+    from paper_2405_10923_gb300 import torch_api as ta
+
+    rh.load()
+
+    def metrics(sk, W, out, m):
+        Q, R = out["Q"], out["R"]
+        Z = sk.apply(rh.colmajor(Q.double()), m)
+        G = (Z.t() @ Z).cpu().numpy()
+        orth = float(np.max(np.abs(np.linalg.eigvalsh(np.eye(m) - G))))
+        W64 = W.double()
+        resid = float(torch.linalg.norm(W64 - Q.double() @ R) / torch.linalg.norm(W64))
+        return orth, resid
+
+    def emit(**kw):
+        print(json.dumps(kw), flush=True)
+
+    if "left_small" in a.cases:
+        n, m, k = 4096, 32, 128
+        W = rh.colmajor(torch.tensor(ri.gaussian(n, m, 1001), dtype=torch.float64, device="cuda"))
+        sk = ta.Sketch(n, k, rh.GAUSSIAN, 2001, rh.F64)
+        opts = ta.make_opts(alg=rh.ALG_LEFT)
+        out = ta.factor(sk, W, opts=opts)
+        ms = _time(lambda: ta.factor(sk, W, opts=opts, out=out, ws=out["ws"]), max(a.reps, 20))
+        orth, resid = metrics(sk, W, out, m)
+        emit(case="left_small", path="left-looking RHQR float64", n=n, m=m, k=k, sketch="gaussian f64",
+             us_per_factorisation=ms * 1e3, orth=orth, resid=resid)
+        sk.close()
+
+    n, m, k = 1 << 20, 128, 512
+    W64 = None
+    if "srht_left" in a.cases or "srht_rec" in a.cases:
+        W64 = ri.device_spectrum(n, m, 1e12, 1002, dtype=torch.float64)
+        W32 = ri.device_spectrum(n, m, 1e12, 1002, dtype=torch.float32)
+        sk = ta.Sketch(n, k, rh.SRHT, 2002)
+    if "srht_left" in a.cases:
+        for W, name in ((W64, "f64"), (W32, "f32")):
+            opts = ta.make_opts(alg=rh.ALG_LEFT)
+            out = ta.factor(sk, W, opts=opts)
+            ms = _time(lambda: ta.factor(sk, W, opts=opts, out=out, ws=out["ws"]), a.reps)
+            orth, resid = metrics(sk, W, out, m)
+            es = W.element_size()
+            emit(case="srht_left", path="left-looking RHQR " + name, n=n, m=m, k=k, sketch="srht",
+                 ms=ms, gbps_w_factored=n * m * es / (ms * 1e-3) / 1e9,
+                 u_traffic_gb=n * (m * (m - 1) / 2 + 3 * m) * es / 1e9, orth=orth, resid=resid)
+    if "srht_rec" in a.cases:
+        for W, name, passes in ((W64, "f64", 2), (W32, "f32", 3)):
+            opts = ta.make_opts(alg=rh.ALG_REC, passes=passes)
+            out = ta.factor(sk, W, opts=opts)
+            ms = _time(lambda: ta.factor(sk, W, opts=opts, out=out, ws=out["ws"]), a.reps)
+            orth, resid = metrics(sk, W, out, m)
+            es = W.element_size()
+            emit(case="srht_rec", path=f"recRHQR {name}, {passes} passes", n=n, m=m, k=k, sketch="srht", ms=ms,
+                 gbps_w_factored=n * m * es / (ms * 1e-3) / 1e9, orth=orth, resid=resid)
+    if "arnoldi" in a.cases:
+        g = 1024
+        n, mmax, k = g * g, 100, 400
+        sk = ta.Sketch(n, k, rh.SRHT, 2005)
+        for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+            b = torch.tensor(np.random.default_rng(1005).standard_normal(n), dtype=dt, device="cuda")
+            arn = ta.Arnoldi(sk, n, mmax, dtype=dt)
+
+            def cycle():
+                _, q = arn.begin(b)
+                for _ in range(mmax):
+                    _, q = arn.step(ri.stencil_apply(q, g))
+                return q
+
+            # rebuild the handle each cycle (begin restarts it)
+            ms = _time(cycle, a.reps)
+            U, S, T, cnt = arn.export()
+            emit(case="arnoldi", path=f"RHQR-Arnoldi {name} basis", n=n, steps=mmax, k=k, sketch="srht",
+                 ms_per_cycle=ms, us_per_step=ms * 1e3 / mmax, reflectors=cnt,
+                 basis_gb=n * (mmax + 1) * b.element_size() / 1e9)
+            arn.close()
+        sk.close()
+
+
+if __name__ == "__main__":
+    main()
