@@ -99,8 +99,44 @@ __device__ __forceinline__ T refresh_row(const ColArgs &a, int64_t i, const doub
   return w;
 }
 
-// SRHT: block j1 owns rows [j1 N2, (j1+1) N2); refresh, signs, FWHT, keep samples
+// Refresh of column j over all rows with the whole GPU (one row per thread,
+// grid-stride): w_j <- w_j - U_{j-1} c (the previous columns read with four
+// independent partial sums), the deferred scaling of column j-1, and the exact
+// top rows of the sketch.
 template <class T>
+__global__ void __launch_bounds__(256) left_refresh_kernel(ColArgs a) {
+  __shared__ double c_s[1024];
+  for (int l = threadIdx.x; l < a.j; l += blockDim.x) c_s[l] = a.c[l];
+  const T inv_g = (a.j >= 1) ? (T)(1.0 / a.gamma[a.j - 1]) : T(1);
+  __syncthreads();
+  const T *W = (const T *)a.W;
+  T *U = (T *)a.U;
+  const int j = a.j;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
+    int l = 0;
+    for (; l + 4 < j; l += 4) {
+      p0 += U[(int64_t)l * a.ldu + i] * (T)c_s[l];
+      p1 += U[(int64_t)(l + 1) * a.ldu + i] * (T)c_s[l + 1];
+      p2 += U[(int64_t)(l + 2) * a.ldu + i] * (T)c_s[l + 2];
+      p3 += U[(int64_t)(l + 3) * a.ldu + i] * (T)c_s[l + 3];
+    }
+    for (; l + 1 < j; ++l) p0 += U[(int64_t)l * a.ldu + i] * (T)c_s[l];
+    T w = W[(int64_t)j * a.ldw + i] - ((p0 + p1) + (p2 + p3));
+    if (j >= 1) {
+      T *up = U + (int64_t)(j - 1) * a.ldu + i;
+      const T u = (i < j - 1) ? T(0) : ((i == j - 1 && a.unit) ? T(1) : *up * inv_g);
+      *up = u;
+      w -= u * (T)c_s[j - 1];
+    }
+    U[(int64_t)j * a.ldu + i] = w;
+    if (i < a.m) a.y[i] = (double)w;
+  }
+}
+
+// SRHT: block j1 owns rows [j1 N2, (j1+1) N2); refresh (or read the refreshed
+// column), signs, FWHT, keep samples
+template <class T, bool REFRESHED>
 __global__ void left_column_srht_kernel(ColArgs a, const uint32_t *sign_bits, int32_t N2, const int32_t *i2_list,
                                         int32_t d2, T *Ystage) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -114,11 +150,18 @@ __global__ void left_column_srht_kernel(ColArgs a, const uint32_t *sign_bits, in
     int64_t i = row0 + t;
     T val = T(0);
     if (i < a.n) {
-      T w = refresh_row<T>(a, i, c_s, inv_g);
-      if (i < a.m) {
-        a.y[i] = (double)w;
+      if (REFRESHED) {
+        if (i >= a.m) {
+          const T w = ((const T *)a.U)[(int64_t)a.j * a.ldu + i];
+          val = ((sign_bits[i >> 5] >> (i & 31)) & 1u) ? -w : w;
+        }
       } else {
-        val = ((sign_bits[i >> 5] >> (i & 31)) & 1u) ? -w : w;
+        T w = refresh_row<T>(a, i, c_s, inv_g);
+        if (i < a.m) {
+          a.y[i] = (double)w;
+        } else {
+          val = ((sign_bits[i >> 5] >> (i & 31)) & 1u) ? -w : w;
+        }
       }
     }
     v[t] = val;
@@ -308,11 +351,14 @@ static rhqr_status left_typed(const SketchView &s, const T *W, int64_t n, int32_
     }
     ca.j = j;
     if (s.kind == RHQR_SKETCH_SRHT) {
+      // refresh with the whole GPU, then sign / transform / sample the refreshed column
+      left_refresh_kernel<T><<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8), 256, 0, st>>>(ca);
+      RHQR_LAUNCH_CHECK();
       size_t smem = (size_t)s.N2 * sizeof(T);
       if (smem > 48 * 1024)
-        RHQR_CUDA_TRY(cudaFuncSetAttribute(left_column_srht_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-      left_column_srht_kernel<T><<<s.N1, 512, smem, st>>>(ca, s.sign_bits, s.N2, s.i2_list, s.d2, (T *)stage);
+        RHQR_CUDA_TRY(cudaFuncSetAttribute(left_column_srht_kernel<T, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      left_column_srht_kernel<T, true><<<s.N1, 512, smem, st>>>(ca, s.sign_bits, s.N2, s.i2_list, s.d2, (T *)stage);
       RHQR_LAUNCH_CHECK();
       left_srht_combine_kernel<T><<<(unsigned)ceil_div(s.k, 128), 128, 0, st>>>(
           (const T *)stage, s.N1, s.d2, s.sample_i1, s.sample_slot, s.k, m, scale, y);
@@ -463,12 +509,14 @@ static rhqr_status arnoldi_reflect(ArnoldiState &a, const T *w, double *h, rhqr_
   ColArgs ca{Wbase, a.n, a.U, a.ldu, a.n, M, J, a.c, a.gamma, a.y, a.scaling == 0 ? 1 : 0};
   const double scale = 1.0 / sqrt((double)a.view.k);
   if (a.view.kind == RHQR_SKETCH_SRHT) {
+    left_refresh_kernel<T><<<(unsigned)std::min<int64_t>(ceil_div(a.n, 256), 152 * 8), 256, 0, st>>>(ca);
+    RHQR_LAUNCH_CHECK();
     size_t smem = (size_t)a.view.N2 * sizeof(T);
     if (smem > 48 * 1024)
-      RHQR_CUDA_TRY(
-          cudaFuncSetAttribute(left_column_srht_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    left_column_srht_kernel<T><<<a.view.N1, 512, smem, st>>>(ca, a.view.sign_bits, a.view.N2, a.view.i2_list,
-                                                              a.view.d2, (T *)a.stage);
+      RHQR_CUDA_TRY(cudaFuncSetAttribute(left_column_srht_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+    left_column_srht_kernel<T, true><<<a.view.N1, 512, smem, st>>>(ca, a.view.sign_bits, a.view.N2,
+                                                                    a.view.i2_list, a.view.d2, (T *)a.stage);
     RHQR_LAUNCH_CHECK();
     left_srht_combine_kernel<T><<<(unsigned)ceil_div(a.view.k, 128), 128, 0, st>>>(
         (const T *)a.stage, a.view.N1, a.view.d2, a.view.sample_i1, a.view.sample_slot, a.view.k, M, scale, a.y);
