@@ -268,6 +268,41 @@ rhqr_status rhqr_batch_get_tuning(rhqr_batch b, int32_t *choice /* host, 3 */);
 rhqr_status rhqr_batch_set_tuning(rhqr_batch b, const int32_t *choice /* host, 3 */);
 
 /*
+ * Factorisation stream for matrices held in host memory (no counterpart in the
+ * paper, which factors a matrix where the arithmetic runs).  Each submission
+ * is one rhqr_factor (Algorithm 4 or 6, options as bound at create) of a host
+ * W into host Q and R; the transfers of consecutive submissions overlap with
+ * each other's factorisation.
+ *   create : binds the sketch, W's dtype wt (F64 or F32), shape n x m and the
+ *            options (NULL = defaults; want_Q must be 1), and allocates `depth`
+ *            (1..4; 2 suffices for overlap) device buffer sets -- W, Q, U when
+ *            needed, S, T, R, info and the rhqr_factor workspace each -- plus
+ *            three non-blocking streams (copy in, compute, copy out).  The
+ *            sketch must outlive the pipeline.
+ *   submit : enqueues the copy of W (host, n x m column-major, ldw >= n) to a
+ *            free buffer set, the factorisation, and the copies of Q (host,
+ *            ldq >= n), R (host, m x m float64, ld = m) and, when not NULL, S
+ *            (host, (k+m) x m float64, lds >= k+m), T (host, m x m) and info
+ *            (host rhqr_info) back.  It returns once the work is enqueued: the
+ *            host buffers must stay valid and unchanged (W) or unread (outputs)
+ *            until rhqr_pipeline_wait returns.  Page-locked host buffers
+ *            (cudaHostAlloc / cudaHostRegister) are needed for the copies to
+ *            overlap; pageable ones give the same results, serialised.
+ *            Argument errors of the factorisation are returned here.
+ *   wait   : blocks until every submitted factorisation's outputs are in host
+ *            memory; a device-side status (breakdown, non-finite) is in info.
+ *   destroy: waits, then frees the buffers, streams and events.
+ * One pipeline is driven by one host thread at a time.
+ */
+typedef struct rhqr_pipeline_s *rhqr_pipeline;
+rhqr_status rhqr_pipeline_create(rhqr_sketch s, int32_t wt, int64_t n, int32_t m, const rhqr_opts *opts,
+                                 int32_t depth, rhqr_pipeline *out);
+rhqr_status rhqr_pipeline_submit(rhqr_pipeline p, const void *W, int64_t ldw, void *Q, int64_t ldq, double *R,
+                                 double *S, int64_t lds, double *T, rhqr_info *info);
+rhqr_status rhqr_pipeline_wait(rhqr_pipeline p);
+rhqr_status rhqr_pipeline_destroy(rhqr_pipeline p);
+
+/*
  * rhqr_sketch_apply_noalloc -- rhqr_sketch_apply (Algorithm 1) without a
  * caller workspace; the paper has no counterpart.  For callers that cannot
  * allocate device memory when they call: code running inside a CUDA-graph

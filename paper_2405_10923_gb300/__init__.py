@@ -103,6 +103,10 @@ _SIGNATURES = {
     "rhqr_batch_tune": (_i32, [_p, _p, _sz, _p, _i32, _p, _p]),
     "rhqr_batch_get_tuning": (_i32, [_p, _p]),
     "rhqr_batch_set_tuning": (_i32, [_p, _p]),
+    "rhqr_pipeline_create": (_i32, [_p, _i32, _i64, _i32, ctypes.POINTER(rhqr_opts), _i32, ctypes.POINTER(_p)]),
+    "rhqr_pipeline_submit": (_i32, [_p, _p, _i64, _p, _i64, _p, _p, _i64, _p, _p]),
+    "rhqr_pipeline_wait": (_i32, [_p]),
+    "rhqr_pipeline_destroy": (_i32, [_p]),
     "rhqr_launch_count": (_i64, []),
     "rhqr_profile_enable": (None, [_i32]),
     "rhqr_profile_read": (_i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
@@ -340,6 +344,27 @@ def rhqr_reconstruct(s, S, lds, T, R, Z, ldz, W, wt, n, m, ldw, U, ldu, Q, ldq, 
     _check("rhqr_reconstruct", load().rhqr_reconstruct(s, _ptr(S), lds, _ptr(T), _ptr(R), _ptr(Z), ldz, _ptr(W), wt, n,
                                                        m, ldw, _ptr(U), ldu, _ptr(Q), ldq, _ptr(ws), ws_bytes,
                                                        _stream(stream)))
+
+
+def rhqr_pipeline_create(s, wt, n, m, opts, depth=2) -> int:
+    out = _p()
+    _check("rhqr_pipeline_create", load().rhqr_pipeline_create(s, wt, n, m, ctypes.byref(opts) if opts else None, depth,
+                                                               ctypes.byref(out)))
+    return out.value
+
+
+def rhqr_pipeline_submit(p, W, ldw, Q, ldq, R, S=None, lds=0, T=None, info=None) -> None:
+    """W, Q, R, S, T, info: host buffers (CPU tensors or addresses)."""
+    _check("rhqr_pipeline_submit", load().rhqr_pipeline_submit(p, _ptr(W), ldw, _ptr(Q), ldq, _ptr(R), _ptr(S), lds,
+                                                               _ptr(T), _ptr(info)))
+
+
+def rhqr_pipeline_wait(p) -> None:
+    _check("rhqr_pipeline_wait", load().rhqr_pipeline_wait(p))
+
+
+def rhqr_pipeline_destroy(p) -> None:
+    _check("rhqr_pipeline_destroy", load().rhqr_pipeline_destroy(p))
 
 
 def rhqr_launch_count() -> int:

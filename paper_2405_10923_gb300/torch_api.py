@@ -12,11 +12,12 @@ import torch
 from . import (ALG_LEFT, ALG_REC, BF16, F16, F32, F64, GAUSSIAN, SRHT, colmajor, dtype_code, ld_of, read_info,
                rhqr_batch_create, rhqr_batch_destroy, rhqr_batch_get_tuning, rhqr_batch_set_tuning, rhqr_batch_tune,
                rhqr_batch_workspace_size, rhqr_factor_batched, rhqr_arnoldi_begin, rhqr_arnoldi_create, rhqr_arnoldi_destroy, rhqr_arnoldi_export, rhqr_arnoldi_step,
-               rhqr_default_opts, rhqr_factor, rhqr_reconstruct, rhqr_sketch_apply, rhqr_sketch_apply_workspace,
+               rhqr_default_opts, rhqr_factor, rhqr_pipeline_create, rhqr_pipeline_destroy, rhqr_pipeline_submit,
+               rhqr_pipeline_wait, rhqr_reconstruct, rhqr_sketch_apply, rhqr_sketch_apply_workspace,
                rhqr_sketch_create, rhqr_sketch_destroy, rhqr_sketch_export, rhqr_sketch_shape, rhqr_workspace_size)
 
 TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}
-__all__ = ["Sketch", "Arnoldi", "Batch", "factor", "reconstruct", "colmajor", "ALG_LEFT", "ALG_REC", "GAUSSIAN", "SRHT"]
+__all__ = ["Sketch", "Arnoldi", "Batch", "Pipeline", "factor", "reconstruct", "colmajor", "ALG_LEFT", "ALG_REC", "GAUSSIAN", "SRHT"]
 
 
 class Sketch:
@@ -102,6 +103,42 @@ def factor(sk: Sketch, W: torch.Tensor, opts=None, out=None, ws: Workspace | Non
                 out["info"], stream)
     out["ws"] = ws
     return out
+
+
+class Pipeline:
+    """Owner of an rhqr_pipeline handle: host W in, host Q and R out, the
+    transfers of consecutive submissions overlapped with the factorisations."""
+
+    def __init__(self, sk: Sketch, n: int, m: int, dtype=torch.float32, opts=None, depth: int = 2):
+        self.sk, self.n, self.m, self.dtype = sk, n, m, dtype
+        self.handle = rhqr_pipeline_create(sk.handle, dtype_code(torch.empty(0, dtype=dtype)), n, m, opts, depth)
+
+    @staticmethod
+    def host_colmajor(rows: int, cols: int, dtype, pin: bool = True) -> torch.Tensor:
+        """A page-locked host tensor of shape (rows, cols) in column-major order."""
+        return torch.empty((cols, rows), dtype=dtype, pin_memory=pin).t()
+
+    def submit(self, W: torch.Tensor, Q: torch.Tensor, R: torch.Tensor, S=None, T=None, info=None):
+        """Enqueue one factorisation; W, Q (column-major, n x m), R (m x m, read
+        as column-major) and the optional S, T, info are host tensors."""
+        for t in (W, Q, R, S, T, info):
+            if t is not None and t.device.type != "cpu":
+                raise ValueError("pipeline buffers are host tensors")
+        rhqr_pipeline_submit(self.handle, W, ld_of(W), Q, ld_of(Q), R, S, ld_of(S) if S is not None else 0, T, info)
+
+    def wait(self):
+        rhqr_pipeline_wait(self.handle)
+
+    def close(self):
+        if self.handle:
+            rhqr_pipeline_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def reconstruct(sk: Sketch, S, T, R, Z, W, want_Q=True):

@@ -45,3 +45,9 @@ def test_argument_errors_are_synchronous():
     assert rh.load().rhqr_batch_destroy(None) == 0
     with pytest.raises(rh.RHQRError):
         rh.rhqr_batch_set_tuning(None, (512, 64, 0))
+    # pipelines: null handles and buffers are rejected on the host
+    assert rh.load().rhqr_pipeline_create(None, rh.F32, 100, 4, None, 2, ctypes.byref(out)) == 1
+    assert rh.load().rhqr_pipeline_create(None, rh.F32, 100, 4, None, 2, None) == 1
+    assert rh.load().rhqr_pipeline_submit(None, None, 0, None, 0, None, None, 0, None, None) == 1
+    assert rh.load().rhqr_pipeline_wait(None) == 1
+    assert rh.load().rhqr_pipeline_destroy(None) == 0
