@@ -171,9 +171,12 @@ rhqr_status rhqr_sketch_create(int64_t n, int32_t k, int32_t kind, uint64_t seed
     // rows padded to 16 bytes (TMA-compatible strides)
     int64_t ldg = (int64_t)align_up((size_t)n * es, 16) / (int64_t)es;
     v.ldg = ldg;
+    // 16-bit operators feed the tensor-core sketch, which reads them in tile order
+    const bool tiles = omega_dtype == RHQR_BF16 || omega_dtype == RHQR_F16;
     Carver c(nullptr, 0);
     c.take<char>((size_t)k * ldg * es);
     c.take<double>(32);
+    if (tiles) c.take<char>(operator_tiles_bytes(n, k));
     s->mem_bytes = c.used() + 256;
     if (cudaMalloc(&s->mem, s->mem_bytes) != cudaSuccess) {
       (void)cudaGetLastError();
@@ -183,9 +186,13 @@ rhqr_status rhqr_sketch_create(int64_t n, int32_t k, int32_t kind, uint64_t seed
     Carver d(s->mem, s->mem_bytes);
     char *gmem = d.take<char>((size_t)k * ldg * es);
     double *coef = d.take<double>(32);
+    char *gt = tiles ? d.take<char>(operator_tiles_bytes(n, k)) : nullptr;
     v.G = gmem;
+    v.Gt = gt;
+    v.gt_nkb = tiles ? operator_tiles_nkb(n) : 0;
     if (ldg != n) RHQR_CUDA_TRY(cudaMemsetAsync(gmem, 0, (size_t)k * ldg * es, st));
     rhqr_status r = make_gaussian_operator(n, k, seed, omega_dtype, gmem, ldg, coef, st);
+    if (r == RHQR_OK && tiles) r = make_operator_tiles(gmem, ldg, n, k, gt, st);
     if (r != RHQR_OK) {
       cudaFree(s->mem);
       delete s;

@@ -19,6 +19,10 @@ struct SketchView {
   // Gaussian: k x n row-major values (ld = ldg) in omega_dtype
   const void *G;
   int64_t ldg;
+  // 16-bit Gaussian operators also in tensor-core tile order (sketch_tc.cu):
+  // 256 x 64 tiles of 32 KiB, tile (t, b) at byte (t * gt_nkb + b) * 32768
+  const void *Gt;
+  int64_t gt_nkb;
 };
 
 size_t sketch_apply_workspace_bytes(const SketchView &s, int32_t m, int32_t xt, int64_t n, int32_t c);

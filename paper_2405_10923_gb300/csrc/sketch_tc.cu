@@ -12,16 +12,22 @@
 // tensor memory and updated with round-to-nearest adds; the per-chunk results
 // are summed in float64 in a fixed order.
 //
-// One CTA owns a 256 x Nt output tile (two M = 128 accumulators, Nt <= 128
-// columns) and one K-chunk of X rows.
-//   warp 0       : TMA producer: G tile (256 x 64 bf16, 128-byte swizzle) and
-//                  X tile (64 rows x Nt float32) per stage
+// One CTA owns a 256 x Nt output tile (Nt <= 128 columns) and one K-chunk of
+// X rows.  The tile is accumulated transposed: tensor-memory lane = column of
+// X (the limbs are the M = 128 operand), accumulator column = row of G (the G
+// tile is the N = 256 operand), so one MMA per 16 rows and limb reads G once
+// for both halves of the tile and the accumulator takes 256 of the 512
+// tensor-memory columns, leaving the other 256 for the running sum.
+//   warp 0       : producer: per stage the G tile (256 x 64, one contiguous
+//                  32 KiB bulk copy from the operator's tile-order copy, which
+//                  holds it already in the 128-byte swizzled layout) and the
+//                  X tile (64 rows x Nt float32, TMA)
 //   warp 1       : tensor-memory allocation and the single MMA-issuing thread
 //   warps 2..7   : converters: staged X -> L limbs in the K-major 128-byte
 //                  swizzled layout the MMA reads (rows < m are zeroed)
 //   warps 8..15  : drainers: fresh accumulator + running sum -> running sum;
 //                  at the end the running sums go to a float32 partial
-//                  [chunk][column][row] in global memory
+//                  [chunk][row][column] in global memory
 // Every wait on an mbarrier is bounded; a wait that runs out sets an error
 // flag, the other roles stop, TMA copies still in flight are awaited (bounded)
 // and tensor memory is released before the block exits.
@@ -48,11 +54,13 @@ constexpr int RUN_COL = 256;            // tensor-memory column of the running s
 
 struct Params {
   int64_t n;
-  int32_t m, m8, c, Nt, k;
+  int32_t m, m64, c, Nt, k;
   int64_t kchunk;
   int32_t limbs, stages, kdrain;
   int32_t xbytes;  // bytes of one X box: 64 rows x Nt columns of float32
-  float *part;  // [nch][c][k]
+  float *part;  // [nch][k][c]
+  const char *gt;  // operator tiles (256 x 64, 32 KiB each), gt_nkb per row of tiles
+  int64_t gt_nkb;
   int *err;
   long long budget;
 };
@@ -106,6 +114,14 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
           smem_u32(dst)),
       "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
+}
+
+// contiguous bulk copy global -> shared (16-byte aligned, multiple of 16 bytes)
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -210,7 +226,7 @@ struct Limb<__half> {
 
 template <class TL, int L>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
-    sketch_tc_kernel(const __grid_constant__ CUtensorMap tmapG, const __grid_constant__ CUtensorMap tmapX, Params P) {
+    sketch_tc_kernel(const __grid_constant__ CUtensorMap tmapX, Params P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   // With up to two limbs, X is split in place: the float32 staging of 8 columns
@@ -229,7 +245,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mt = blockIdx.x, nt = blockIdx.y, ch = blockIdx.z;
   const int col0 = nt * P.Nt;
-  const int64_t x_begin = (int64_t)P.m8 + (int64_t)ch * P.kchunk;
+  // chunks start on 64-row boundaries (whole operator tiles); rows below m
+  // (the exact top block) are zeroed by the converters
+  const int64_t x_begin = (int64_t)P.m64 + (int64_t)ch * P.kchunk;
   const int64_t x_end = min(P.n, x_begin + P.kchunk);
   const int steps = (int)((x_end - x_begin + BK - 1) / BK);
   const int per_drain = P.kdrain / BK;
@@ -271,7 +289,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         uint8_t *st = smem + s * stage_bytes;
         mbar_expect_tx(full_a + s, (uint32_t)(A_BYTES + P.xbytes));
         const int xr = (int)(x_begin + (int64_t)i * BK);
-        tma_load_2d(st, &tmapG, full_a + s, xr, mt * BM);
+        bulk_load(st, P.gt + ((int64_t)mt * P.gt_nkb + xr / BK) * A_BYTES, A_BYTES, full_a + s);
         tma_load_2d(st + A_BYTES, &tmapX, full_a + s, xr, col0);
         ++issued;
       }
@@ -285,7 +303,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(128, P.Nt, Limb<TL>::fmt);
+      const uint32_t idesc = make_idesc(128, BM, Limb<TL>::fmt);  // M: 128 columns of X, N: 256 rows of G
       int i = 0;
       for (int d = 0; d < drains && i < steps; ++d) {
         if (d > 0 && !mbar_wait(fresh_empty, (uint32_t)(d - 1) & 1u, P.budget, P.err, abort_s)) break;
@@ -301,19 +319,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           }
           tc_fence_after();
           // descriptors advance by (byte offset >> 4): the loops unroll to constant adds
-          const uint32_t a_base = smem_u32(smem + s * stage_bytes);
-          const uint64_t ad0 = sw128_desc(a_base);
-          const uint64_t bd0 = INPLACE ? sw128_desc(a_base + A_BYTES, 2048) : sw128_desc(a_base + A_BYTES + X_BYTES);
+          const uint32_t st_base = smem_u32(smem + s * stage_bytes);
+          const uint64_t gd0 = sw128_desc(st_base);  // G: 256 rows of 128 bytes
+          const uint64_t xd0 = INPLACE ? sw128_desc(st_base + A_BYTES, 2048) : sw128_desc(st_base + A_BYTES + X_BYTES);
           constexpr int LIMB_STRIDE = INPLACE ? 1024 : B_BYTES;
 #pragma unroll
-          for (int h = 0; h < 2; ++h)
+          for (int kk = 0; kk < BK / 16; ++kk)
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-#pragma unroll
-              for (int l = 0; l < L; ++l)
-                mma_f16(tmem + (uint32_t)(h * NT), ad0 + (uint64_t)((h * (128 * 128) + kk * 32) >> 4),
-                        bd0 + (uint64_t)((l * LIMB_STRIDE + kk * 32) >> 4), idesc,
-                        (uint32_t)(j != 0 || kk != 0 || l != 0));
+            for (int l = 0; l < L; ++l)
+              mma_f16(tmem, xd0 + (uint64_t)((l * LIMB_STRIDE + kk * 32) >> 4), gd0 + (uint64_t)((kk * 32) >> 4),
+                      idesc, (uint32_t)(j != 0 || kk != 0 || l != 0));
           mma_commit(empty + s);
         }
         mma_commit(fresh_full);
@@ -408,13 +423,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
     }
   } else if (warp >= DRAIN_WARP0) {
-    // drainers: warp -> (half h, lane quarter qd); thread -> one accumulator row
+    // drainers: warp -> (half h of the G rows, lane quarter qd); thread -> one
+    // column of X (tensor-memory lane), 128 accumulator columns (rows of G)
     const int dw = warp - DRAIN_WARP0;
     const int h = dw >> 2, qd = warp & 3;
     const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
-    const uint32_t fresh = tmem + lane_base + (uint32_t)(h * NT);
-    const uint32_t run = tmem + lane_base + (uint32_t)(RUN_COL + h * NT);
-    const int row = mt * BM + h * 128 + qd * 32 + lane;
+    const uint32_t fresh = tmem + lane_base + (uint32_t)(h * 128);
+    const uint32_t run = tmem + lane_base + (uint32_t)(RUN_COL + h * 128);
+    const int cc = col0 + qd * 32 + lane;
+    const bool own_col = qd * 32 + lane < P.Nt && cc < P.c;
+    const int row0 = mt * BM + h * 128;
     bool ok = true;
     for (int d = 0; d < drains; ++d) {
       if (!warp_wait(fresh_full, (uint32_t)d & 1u, P.budget, P.err, abort_s)) {
@@ -423,7 +441,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
       tc_fence_after();
       const bool last = (d == drains - 1);
-      for (int c0 = 0; c0 < P.Nt; c0 += 32) {
+      for (int c0 = 0; c0 < 128; c0 += 32) {
         uint32_t f[32], r[32];
         tmem_ld32(fresh + c0, f);
         if (d > 0) tmem_ld32(run + c0, r);
@@ -435,11 +453,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           r[j] = __float_as_uint(v);
         }
         if (last) {
-          if (row < P.k) {
+          if (own_col) {
             for (int j = 0; j < 32; ++j) {
-              const int cc = col0 + c0 + j;
-              if (cc < P.c && c0 + j < P.Nt)
-                P.part[((int64_t)ch * P.c + cc) * P.k + row] = __uint_as_float(r[j]);
+              const int row = row0 + c0 + j;
+              if (row < P.k) P.part[((int64_t)ch * P.k + row) * P.c + cc] = __uint_as_float(r[j]);
             }
           }
         } else {
@@ -462,22 +479,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 }
 
 template <class TL, int L>
-static rhqr_status launch_sketch(dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap &mapG,
-                                 const CUtensorMap &mapX, const Params &P) {
+static rhqr_status launch_sketch(dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap &mapX, const Params &P) {
   RHQR_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<TL, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  sketch_tc_kernel<TL, L><<<grid, NUM_THREADS, smem, st>>>(mapG, mapX, P);
+  sketch_tc_kernel<TL, L><<<grid, NUM_THREADS, smem, st>>>(mapX, P);
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }
 
-// Z[ztop + r, c] = scale * sum_chunk part[chunk][c][r]  (float64, fixed order)
+// Z[ztop + r, col] = scale * sum_chunk part[chunk][r][col]  (float64, fixed order)
 __global__ void reduce_part_kernel(const float *part, int32_t nch, int32_t k, int32_t c, int32_t ztop, double scale,
                                    double *Z, int64_t ldz) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)k * c) return;
   double acc = 0.0;
   for (int ch = 0; ch < nch; ++ch) acc += (double)part[(int64_t)ch * k * c + idx];
-  int64_t col = idx / k, r = idx - col * k;
+  int64_t r = idx / c, col = idx - r * c;
   Z[col * ldz + ztop + r] = acc * scale;
 }
 
@@ -488,7 +504,51 @@ __global__ void copy_top_f32_kernel(const float *X, int64_t ldx, int32_t m, int3
   Z[col * ldz + i] = (double)X[col * ldx + i];
 }
 
+// One 16-byte chunk (8 values of one row) per thread: row r, chunk q of the
+// operator go to tile (r / 256, q / 8), tile row r % 256, position
+// (q % 8) ^ (r % 8); chunks past k or n are written as zeros.
+__global__ void operator_tiles_kernel(const uint16_t *G, int64_t ldg, int64_t n, int32_t k, int64_t nkb,
+                                      uint4 *Gt) {
+  const int64_t nq = nkb * 8;  // chunks per padded row
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t rows = (int64_t)((k + BM - 1) / BM) * BM;
+  if (idx >= rows * nq) return;
+  const int64_t r = idx / nq, q = idx - r * nq;
+  uint4 w;
+  if (r < k && q * 8 + 8 <= n) {
+    w = *reinterpret_cast<const uint4 *>(G + r * ldg + q * 8);  // rows are 16-byte aligned (ldg)
+  } else {
+    uint16_t v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int64_t col = q * 8 + e;
+      v[e] = (r < k && col < n) ? G[r * ldg + col] : (uint16_t)0;
+    }
+    w = make_uint4((uint32_t)v[0] | ((uint32_t)v[1] << 16), (uint32_t)v[2] | ((uint32_t)v[3] << 16),
+                   (uint32_t)v[4] | ((uint32_t)v[5] << 16), (uint32_t)v[6] | ((uint32_t)v[7] << 16));
+  }
+  const int64_t tile = (r / BM) * nkb + q / 8;
+  const int64_t rr = r % BM;
+  Gt[tile * (A_BYTES / 16) + rr * 8 + ((q % 8) ^ (rr % 8))] = w;
+}
+
 }  // namespace tc
+
+int64_t operator_tiles_nkb(int64_t n) { return ceil_div(n, (int64_t)tc::BK); }
+
+size_t operator_tiles_bytes(int64_t n, int32_t k) {
+  return (size_t)ceil_div((int64_t)k, (int64_t)tc::BM) * (size_t)operator_tiles_nkb(n) * tc::A_BYTES;
+}
+
+rhqr_status make_operator_tiles(const void *G, int64_t ldg, int64_t n, int32_t k, void *Gt, cudaStream_t st) {
+  if (n < 1 || k < 1 || ldg < n || (ldg * 2) % 16 != 0 || ((uintptr_t)G % 16) != 0) return RHQR_EINVAL;
+  const int64_t nkb = operator_tiles_nkb(n);
+  const int64_t total = ceil_div((int64_t)k, (int64_t)tc::BM) * tc::BM * nkb * 8;
+  tc::operator_tiles_kernel<<<(unsigned)ceil_div(total, (int64_t)256), 256, 0, st>>>((const uint16_t *)G, ldg, n, k,
+                                                                                      nkb, (uint4 *)Gt);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
+}
 
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -508,7 +568,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // Work split: the CTAs of one launch cover (k/256) x (c/Nt) tiles times nch
 // K-chunks; nch is chosen so the grid fills the 152 SMs in whole waves.
 static int64_t tc_nchunks(const SketchView &s, int64_t n, int32_t m, int32_t c, int64_t *kchunk) {
-  int64_t K = n - (m & ~7);
+  int64_t K = n - (m & ~63);
   int64_t Np = ceil_div(c, 16) * 16;
   int64_t tiles = ceil_div(s.k, tc::BM) * ceil_div(Np, tc::NT);
   int64_t want = std::max<int64_t>(1, 152 / std::max<int64_t>(1, tiles));
@@ -523,7 +583,7 @@ bool sketch_tc_supported(const SketchView &s, int64_t n, int32_t m, int32_t c) {
   if (s.kind != RHQR_SKETCH_GAUSSIAN) return false;
   if (s.omega_dtype != RHQR_BF16 && s.omega_dtype != RHQR_F16) return false;
   if (c < 1 || c > tc::MAXC || m < 0 || n <= m || n > (int64_t(1) << 31) - 1) return false;
-  if ((s.ldg * 2) % 16 != 0) return false;
+  if (s.Gt == nullptr || s.gt_nkb != operator_tiles_nkb(n)) return false;
   return tensor_map_encoder() != nullptr;
 }
 
@@ -547,20 +607,7 @@ rhqr_status sketch_apply_tc(const SketchView &s, int32_t m, const float *X, int6
 
   const int32_t Np = (int32_t)ceil_div(c, 16) * 16;
   const int32_t Nt = std::min<int32_t>(tc::NT, Np);
-  CUtensorMap mapG, mapX;
-  {
-    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)s.k};
-    cuuint64_t strides[1] = {(cuuint64_t)s.ldg * 2};
-    cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult cr = tensor_map_encoder()(&mapG,
-                                       s.omega_dtype == RHQR_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                                  : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
-                                       2, const_cast<void *>(s.G), dims, strides, box, estr,
-                                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) return RHQR_ECUDA;
-  }
+  CUtensorMap mapX;
   {
     cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)c};
     cuuint64_t strides[1] = {(cuuint64_t)ldx * 4};
@@ -575,7 +622,7 @@ rhqr_status sketch_apply_tc(const SketchView &s, int32_t m, const float *X, int6
   tc::Params P;
   P.n = n;
   P.m = m;
-  P.m8 = m & ~7;
+  P.m64 = m & ~63;
   P.c = c;
   P.Nt = Nt;
   P.k = s.k;
@@ -585,6 +632,8 @@ rhqr_status sketch_apply_tc(const SketchView &s, int32_t m, const float *X, int6
   P.kdrain = tc::KDRAIN;
   P.xbytes = tc::BK * Nt * 4;
   P.part = part;
+  P.gt = (const char *)s.Gt;
+  P.gt_nkb = s.gt_nkb;
   P.err = err;
   P.budget = 4000000LL;
   const size_t stage_bytes = tc::A_BYTES + tc::X_BYTES + (limbs <= 2 ? 0 : (size_t)limbs * tc::B_BYTES);
@@ -592,15 +641,15 @@ rhqr_status sketch_apply_tc(const SketchView &s, int32_t m, const float *X, int6
   dim3 grid((unsigned)ceil_div(s.k, tc::BM), (unsigned)ceil_div(Np, Nt), (unsigned)nch);
   if (s.omega_dtype == RHQR_BF16) {
     switch (limbs) {
-      case 1: RHQR_TRY((tc::launch_sketch<__nv_bfloat16, 1>(grid, smem, st, mapG, mapX, P))); break;
-      case 2: RHQR_TRY((tc::launch_sketch<__nv_bfloat16, 2>(grid, smem, st, mapG, mapX, P))); break;
-      default: RHQR_TRY((tc::launch_sketch<__nv_bfloat16, 3>(grid, smem, st, mapG, mapX, P))); break;
+      case 1: RHQR_TRY((tc::launch_sketch<__nv_bfloat16, 1>(grid, smem, st, mapX, P))); break;
+      case 2: RHQR_TRY((tc::launch_sketch<__nv_bfloat16, 2>(grid, smem, st, mapX, P))); break;
+      default: RHQR_TRY((tc::launch_sketch<__nv_bfloat16, 3>(grid, smem, st, mapX, P))); break;
     }
   } else {
     switch (limbs) {
-      case 1: RHQR_TRY((tc::launch_sketch<__half, 1>(grid, smem, st, mapG, mapX, P))); break;
-      case 2: RHQR_TRY((tc::launch_sketch<__half, 2>(grid, smem, st, mapG, mapX, P))); break;
-      default: RHQR_TRY((tc::launch_sketch<__half, 3>(grid, smem, st, mapG, mapX, P))); break;
+      case 1: RHQR_TRY((tc::launch_sketch<__half, 1>(grid, smem, st, mapX, P))); break;
+      case 2: RHQR_TRY((tc::launch_sketch<__half, 2>(grid, smem, st, mapX, P))); break;
+      default: RHQR_TRY((tc::launch_sketch<__half, 3>(grid, smem, st, mapX, P))); break;
     }
   }
   if (m > 0) {

@@ -26,7 +26,8 @@
 // tile (counters in its shared memory that the peer increments).
 //
 // Warp roles: warp 0 issues the MMAs (one thread), warp 1 owns tensor memory,
-// warp 2 loads X by TMA (64-column boxes of a tile, two stages) when X and its
+// warp 2 loads X by TMA (64-column boxes of a tile, two stages, each box of the
+// next tile prefetched into L2 when this one is loaded) when X and its
 // leading dimension are 16-byte aligned, warps 4-11 (two groups, one per A
 // stage) scale, split and store the limbs to tensor memory (thread = row =
 // tensor-memory lane), warps 12-15 drain the accumulator into shared memory
@@ -325,6 +326,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           tc::mbar_expect_tx(x_full + s, (uint32_t)XST_BYTES);
           tc::tma_load_2d(xst + s * (XST_BYTES / 4), &tmapX, x_full + s, (int)(t * TILE), kc * 64);
           last_u[s] = (int)u;
+          // two shared-memory stages hold too few bytes to cover DRAM latency: the
+          // same chunk of this CTA's next tile is brought into L2 a tile ahead
+          if (t + tstep < ntiles) tc::tma_prefetch_2d(&tmapX, (int)((t + tstep) * TILE), kc * 64);
         }
       if (!ok) {  // wait (bounded) for the copies still in flight before the CTA exits
         for (int s = 0; s < 2; ++s) {

@@ -26,6 +26,11 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const void *map, uint64_t
       "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+// Prefetch of the box at (x, y) into L2 (no shared memory, no completion)
+__device__ __forceinline__ void tma_prefetch_2d(const void *map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"((uint64_t)map), "r"(x), "r"(y)
+               : "memory");
+}
 // 2-D tiled TMA store of a shared-memory box to (x = inner, y); bulk-group completion
 __device__ __forceinline__ void tma_store_2d(const void *map, const void *src, int x, int y) {
   asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"((uint64_t)map),

@@ -29,7 +29,8 @@ def _np(t):
 
 @pytest.mark.parametrize("dt", ["bf16", "f16"])
 @pytest.mark.parametrize("n,m,c,k", [(50000, 16, 16, 1024), (40003, 13, 40, 300), (70000, 256, 256, 512),
-                                     (9000, 0, 7, 256), (20000, 5, 256, 1024)])
+                                     (9000, 0, 7, 256), (20000, 5, 256, 1024), (30001, 100, 100, 256),
+                                     (12345, 70, 129, 640)])
 def test_tc_sketch_matches_oracle(gpu_lib, dt, n, m, c, k):
     from paper_2405_10923_gb300 import torch_api as ta
 
