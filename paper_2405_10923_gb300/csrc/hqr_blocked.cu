@@ -50,14 +50,17 @@ __global__ void __launch_bounds__(PT) hqr_panel_kernel(Args a) {
   const int64_t p = a.p;
   const int64_t row0 = (int64_t)j0 + (int64_t)rank * per;
   const int nloc = (int)clamp64(p - row0, 0, per);
-  double *pan = sm;                      // [NB][per]: column c, local row i
-  double *part = sm + NB * per;          // [MAXCS][NB + 1]: partial sums pushed by every CTA
-  double *gram = part + MAXCS * (NB + 1);  // [NB][NB]: partial V^t V of this CTA
+  const int ps = per | 1;  // odd column stride: lanes reading one row of 32 columns hit distinct banks
+  double *pan = sm;                      // [NB][ps]: column c, local row i
+  double *part = sm + NB * ps;           // [MAXCS][NB + 1]: partial sums pushed by every CTA
+  double *gram = part + MAXCS * (NB + 1);  // [NB][NB]: gram[k * NB + l] = v_k . v_l (k < l), whole cluster
   double *wsh = gram + NB * NB;          // [NB]
   double *zsh = wsh + NB;                // [1]: z_jj pushed by its owner
+  double *Ts = zsh + 2;                  // [NB][NB]: the panel's T (rank 0), column-major
+  double *red = Ts + NB * NB;            // [PT / 32][32]: per-warp partial dots
   for (int e = tid; e < nbp * per; e += PT) {
     const int c = e / per, i = e % per;
-    pan[c * per + i] = i < nloc ? a.A[(int64_t)(j0 + c) * p + row0 + i] : 0.0;
+    pan[c * ps + i] = i < nloc ? a.A[(int64_t)(j0 + c) * p + row0 + i] : 0.0;
   }
   __syncthreads();
   for (int jc = 0; jc < nbp; ++jc) {
@@ -70,11 +73,11 @@ __global__ void __launch_bounds__(PT) hqr_panel_kernel(Args a) {
     const uint32_t owner = (uint32_t)(jc / per);
     if (warp == 0) {
       double ss = 0.0;
-      for (int i = lo + lane; i < nloc; i += 32) ss += pan[jc * per + i] * pan[jc * per + i];
+      for (int i = lo + lane; i < nloc; i += 32) ss += pan[jc * ps + i] * pan[jc * ps + i];
       ss = warp_sum(ss);
       if (lane < (int)cs) {
         tc::st_cluster_f64(tc::map_to_rank(part + rank * (NB + 1), (uint32_t)lane), ss);
-        if (rank == owner) tc::st_cluster_f64(tc::map_to_rank(zsh, (uint32_t)lane), pan[jc * per + (jc - (int)owner * per)]);
+        if (rank == owner) tc::st_cluster_f64(tc::map_to_rank(zsh, (uint32_t)lane), pan[jc * ps + (jc - (int)owner * per)]);
       }
     }
     tc::cluster_sync();
@@ -85,22 +88,27 @@ __global__ void __launch_bounds__(PT) hqr_panel_kernel(Args a) {
       tot = warp_sum(tot);
     }
     if (tid == 0) {
-      const double rho = sqrt(tot), zjj = *zsh;
-      const bool fail = !isfinite(rho) || !isfinite(zjj) || rho == 0.0;
+      // one reciprocal square root and one division per column (FP64 square
+      // roots and divisions are long dependent sequences on this GPU)
+      const double zjj = *zsh;
+      const bool zero = tot == 0.0;
+      const double rinv = rsqrt(tot);  // 1 / rho
+      const double rho = tot * rinv;
+      const bool fail = zero || !isfinite(rho) || !isfinite(zjj);
       if (fail) {
         if (rank == 0) {
-          set_status(a.info, rho == 0.0 ? RHQR_EBREAKDOWN : RHQR_ENONFINITE, (int32_t)j);
+          set_status(a.info, zero ? RHQR_EBREAKDOWN : RHQR_ENONFINITE, (int32_t)j);
           *a.bad = 1;
         }
       } else {
         const double sigma = zjj < 0.0 ? -1.0 : 1.0;
         const double gamma = zjj + sigma * rho;
         if (a.scaling == 0) {  // v_j = 1, beta = 1 + |z_jj| / rho
-          sh[0] = 1.0 + fabs(zjj) / rho;
+          sh[0] = 1.0 + fabs(zjj) * rinv;
           sh[1] = 1.0 / gamma;
           sh[2] = 1.0;
         } else {               // ||v|| = sqrt 2, beta = 1
-          const double rdiv = 1.0 / sqrt(rho * (rho + fabs(zjj)));
+          const double rdiv = rsqrt(rho * (rho + fabs(zjj)));
           sh[0] = 1.0;
           sh[1] = rdiv;
           sh[2] = gamma * rdiv;
@@ -120,72 +128,82 @@ __global__ void __launch_bounds__(PT) hqr_panel_kernel(Args a) {
     const double beta = sh[0], rdiv = sh[1], vjj = sh[2];
     for (int i = lo + tid; i < nloc; i += PT) {
       const int64_t gi = row0 + i;
-      pan[jc * per + i] = gi == j ? vjj : pan[jc * per + i] * rdiv;
+      pan[jc * ps + i] = gi == j ? vjj : pan[jc * ps + i] * rdiv;
     }
     __syncthreads();
-    // ---- v . z_c for the panel columns c > j, then z_c -= beta v (v . z_c)
-    for (int c = jc + 1 + warp; c < nbp; c += PT / 32) {
+    // ---- v . z_c for the panel columns c > j (then z_c -= beta v (v . z_c)),
+    //      and v . v_k for the reflectors k < j already formed: column j of the
+    //      panel's V^t V, from which T is built at the end (no second pass over
+    //      the rows).  Rows below j only: v_k and v vanish above their diagonals.
+    //      Lane = column, warp = every 8th own row: no butterfly reductions (FP64
+    //      instructions are the scarce resource); the 8 warp partials of a
+    //      column are added by a fixed tree and pushed to every CTA.
+    {
+      const bool col = lane < nbp && lane != jc;
       double d = 0.0;
-      for (int i = lo + lane; i < nloc; i += 32) d += pan[jc * per + i] * pan[c * per + i];
-      d = warp_sum(d);
-      if (lane < (int)cs) tc::st_cluster_f64(tc::map_to_rank(part + rank * (NB + 1) + 1 + c, (uint32_t)lane), d);
+      if (col)
+        for (int i = lo + warp; i < nloc; i += PT / 32) d += pan[jc * ps + i] * pan[lane * ps + i];
+      red[warp * 32 + lane] = d;
+    }
+    __syncthreads();
+    if (warp == 0 && lane < nbp && lane != jc) {
+      const double *rw = red + lane;
+      const double d = ((rw[0] + rw[32]) + (rw[64] + rw[96])) + ((rw[128] + rw[160]) + (rw[192] + rw[224]));
+      for (uint32_t r = 0; r < cs; ++r) tc::st_cluster_f64(tc::map_to_rank(part + rank * (NB + 1) + 1 + lane, r), d);
     }
     tc::cluster_sync();
-    // w_c = beta * (sum over ranks): half-warps add the 16 (or fewer) partials of a column by a lane tree
-    for (int c2 = jc + 1 + 2 * warp; c2 < nbp; c2 += 2 * (PT / 32)) {  // warp-uniform bound
-      const int c = c2 + (lane >> 4), r = lane & 15;
-      double w = (c < nbp && r < (int)cs) ? part[r * (NB + 1) + 1 + c] : 0.0;
+    // sums over ranks, lane = column, by a fixed tree over the 16 (or fewer)
+    // ranks; w_c = beta * sum for c > j, gram[k][j] = sum for k < j
+    if (warp == 0 && lane < nbp && lane != jc) {
+      double v[MAXCS];
 #pragma unroll
-      for (int o = 8; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-      if (r == 0 && c < nbp) wsh[c] = beta * w;
+      for (int r = 0; r < MAXCS; ++r) v[r] = r < (int)cs ? part[r * (NB + 1) + 1 + lane] : 0.0;
+#pragma unroll
+      for (int h = MAXCS / 2; h > 0; h >>= 1)
+#pragma unroll
+        for (int r = 0; r < h; ++r) v[r] = v[2 * r] + v[2 * r + 1];
+      if (lane > jc) wsh[lane] = beta * v[0];
+      else gram[lane * NB + jc] = v[0];
     }
     __syncthreads();
     for (int e = tid; e < (nbp - jc - 1) * (nloc - lo); e += PT) {
       const int c = jc + 1 + e / (nloc - lo), i = lo + e % (nloc - lo);
-      pan[c * per + i] -= pan[jc * per + i] * wsh[c];
+      pan[c * ps + i] -= pan[jc * ps + i] * wsh[c];
     }
     __syncthreads();
-  }
-  // ---- the panel's T: partial V^t V (V[:, k] vanishes above row j0 + k)
-  for (int q = warp; q < nbp * nbp; q += PT / 32) {
-    const int k = q / nbp, l = q % nbp;
-    if (k >= l) continue;
-    const int lo = (int)clamp64((int64_t)j0 + l - row0, 0, nloc);
-    double d = 0.0;
-    for (int i = lo + lane; i < nloc; i += 32) d += pan[k * per + i] * pan[l * per + i];
-    d = warp_sum(d);
-    if (lane == 0) gram[k * NB + l] = d;
   }
   // write the factored panel back: A (v below the diagonal, R above), S
   for (int e = tid; e < nbp * nloc; e += PT) {
     const int c = e / nloc, i = e % nloc;
     const int64_t gi = row0 + i, j = (int64_t)j0 + c;
-    const double v = pan[c * per + i];
+    const double v = pan[c * ps + i];
     a.A[j * p + gi] = v;
     a.S[j * a.lds + gi] = gi < j ? 0.0 : v;
   }
   if (rank == 0)
     for (int e = tid; e < nbp * j0; e += PT) a.S[(int64_t)(j0 + e / j0) * a.lds + e % j0] = 0.0;
-  tc::cluster_sync();
   if (rank == 0 && warp == 0) {
-    // T column l = -beta_l T[0:l, 0:l] y, y_k = sum over CTAs of gram[k, l]; lane k owns row k
-    double *T = a.Tp;
+    // T column l = -beta_l T[0:l, 0:l] y with y_k = v_k . v_l (gram, already
+    // summed over the cluster); lane k owns row k, T is built in shared memory
+    // and copied out.  Four partial sums shorten the dependent FP64 chain.
+    const double bmine = lane < nbp ? a.beta[j0 + lane] : 0.0;
     for (int l = 0; l < nbp; ++l) {
-      double y = 0.0;
-      if (lane < l)
-        for (uint32_t r = 0; r < cs; ++r) y += tc::ld_cluster_f64(tc::map_to_rank(gram + lane * NB + l, r));
-      wsh[lane] = y;
-      __syncwarp();
-      double t = 0.0;
-      if (lane < l)
-        for (int q = lane; q < l; ++q) t += T[q * NB + lane] * wsh[q];
-      const double bl = a.beta[j0 + l];
-      __syncwarp();
-      if (lane < l) T[l * NB + lane] = -bl * t;
-      if (lane == l) T[l * NB + l] = bl;
-      if (lane > l) T[l * NB + lane] = 0.0;
+      double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+      if (lane < l) {
+        int q = lane;
+        for (; q + 3 < l; q += 4) {
+          t0 += Ts[q * NB + lane] * gram[q * NB + l];
+          t1 += Ts[(q + 1) * NB + lane] * gram[(q + 1) * NB + l];
+          t2 += Ts[(q + 2) * NB + lane] * gram[(q + 2) * NB + l];
+          t3 += Ts[(q + 3) * NB + lane] * gram[(q + 3) * NB + l];
+        }
+        for (; q < l; ++q) t0 += Ts[q * NB + lane] * gram[q * NB + l];
+      }
+      const double bl = __shfl_sync(0xffffffffu, bmine, l);
+      Ts[l * NB + lane] = lane < l ? -bl * ((t0 + t1) + (t2 + t3)) : (lane == l ? bl : 0.0);
       __syncwarp();
     }
+    for (int e = lane; e < nbp * NB; e += 32) a.Tp[e] = Ts[e];
   }
   tc::cluster_sync();  // peers finish reading this CTA's shared memory
 }
@@ -230,7 +248,8 @@ __global__ void hqr_r_kernel(const double *A, int64_t p, int32_t m, const double
 }
 
 static size_t panel_smem(int per) {
-  return sizeof(double) * ((size_t)NB * per + (size_t)MAXCS * (NB + 1) + (size_t)NB * NB + NB + 2);
+  return sizeof(double) * ((size_t)NB * (per | 1) + (size_t)MAXCS * (NB + 1) + (size_t)NB * NB + NB + 2 +
+                           (size_t)NB * NB + (size_t)PT);
 }
 
 // Largest cluster (16, 8 or 4 CTAs) that fits the first panel of p rows.
