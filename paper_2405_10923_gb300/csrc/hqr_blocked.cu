@@ -56,8 +56,7 @@ __global__ void __launch_bounds__(PT) hqr_panel_kernel(Args a) {
   double *gram = part + MAXCS * (NB + 1);  // [NB][NB]: gram[k * NB + l] = v_k . v_l (k < l), whole cluster
   double *wsh = gram + NB * NB;          // [NB]
   double *zsh = wsh + NB;                // [1]: z_jj pushed by its owner
-  double *Ts = zsh + 2;                  // [NB][NB]: the panel's T (rank 0), column-major
-  double *red = Ts + NB * NB;            // [PT / 32][32]: per-warp partial dots
+  double *red = zsh + 2;                 // [PT / 32][32]: per-warp partial dots
   for (int e = tid; e < nbp * per; e += PT) {
     const int c = e / per, i = e % per;
     pan[c * ps + i] = i < nloc ? a.A[(int64_t)(j0 + c) * p + row0 + i] : 0.0;
@@ -182,40 +181,28 @@ __global__ void __launch_bounds__(PT) hqr_panel_kernel(Args a) {
   }
   if (rank == 0)
     for (int e = tid; e < nbp * j0; e += PT) a.S[(int64_t)(j0 + e / j0) * a.lds + e % j0] = 0.0;
-  if (rank == 0 && warp == 0) {
-    // T column l = -beta_l T[0:l, 0:l] y with y_k = v_k . v_l (gram, already
-    // summed over the cluster); lane k owns row k, T is built in shared memory
-    // and copied out.  Four partial sums shorten the dependent FP64 chain.
-    const double bmine = lane < nbp ? a.beta[j0 + lane] : 0.0;
-    for (int l = 0; l < nbp; ++l) {
-      double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
-      if (lane < l) {
-        int q = lane;
-        for (; q + 3 < l; q += 4) {
-          t0 += Ts[q * NB + lane] * gram[q * NB + l];
-          t1 += Ts[(q + 1) * NB + lane] * gram[(q + 1) * NB + l];
-          t2 += Ts[(q + 2) * NB + lane] * gram[(q + 2) * NB + l];
-          t3 += Ts[(q + 3) * NB + lane] * gram[(q + 3) * NB + l];
-        }
-        for (; q < l; ++q) t0 += Ts[q * NB + lane] * gram[q * NB + l];
-      }
-      const double bl = __shfl_sync(0xffffffffu, bmine, l);
-      Ts[l * NB + lane] = lane < l ? -bl * ((t0 + t1) + (t2 + t3)) : (lane == l ? bl : 0.0);
-      __syncwarp();
+  // The panel's T is not formed: with T^{-1} = diag(1/beta) + striu(V^t V) the
+  // trailing update solves with it instead (one warp per update CTA), so the
+  // panel only hands over V^t V (strict upper part, column-major NB x NB).
+  if (rank == 0)
+    for (int e = tid; e < nbp * NB; e += PT) {
+      const int k = e % NB, l = e / NB;
+      a.Tp[e] = k < l ? gram[k * NB + l] : 0.0;
     }
-    for (int e = lane; e < nbp * NB; e += 32) a.Tp[e] = Ts[e];
-  }
   tc::cluster_sync();  // peers finish reading this CTA's shared memory
 }
 
-// Z[:, c] <- Z[:, c] - V T^t V^t Z[:, c] for one trailing column c per CTA
+// Z[:, c] <- Z[:, c] - V T^t V^t Z[:, c] for one trailing column c per CTA,
+// with T^t w found by forward substitution in T^{-t} = diag(1/beta) +
+// striu(V^t V)^t (Tp holds the panel's V^t V, column l = entries (k, l), k < l)
 __global__ void __launch_bounds__(UT) hqr_update_kernel(Args a) {
-  __shared__ double w[NB], w2[NB];
+  __shared__ double w[NB], w2[NB], gsh[NB * NB];
   if (*(volatile int *)a.bad) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t p = a.p, j0 = a.j0;
   const int nbp = a.nbp;
   double *z = a.A + (int64_t)(j0 + nbp + blockIdx.x) * p;
+  for (int e = tid; e < nbp * NB; e += UT) gsh[e] = a.Tp[e];
   for (int k = warp; k < nbp; k += UT / 32) {
     const double *v = a.S + (j0 + k) * a.lds;
     double d = 0.0;
@@ -224,10 +211,17 @@ __global__ void __launch_bounds__(UT) hqr_update_kernel(Args a) {
     if (lane == 0) w[k] = d;
   }
   __syncthreads();
-  if (tid < nbp) {
-    double t = 0.0;
-    for (int q = 0; q <= tid; ++q) t += a.Tp[tid * NB + q] * w[q];  // (T^t w)_tid
-    w2[tid] = t;
+  if (warp == 0) {
+    // w2_q = beta_q (w_q - sum_{k<q} G_kq w2_k); lane i keeps its running sum
+    const double bi = lane < nbp ? a.beta[j0 + lane] : 0.0;
+    const double wi = lane < nbp ? w[lane] : 0.0;
+    double s = 0.0, res = 0.0;
+    for (int q = 0; q < nbp; ++q) {
+      const double t = __shfl_sync(0xffffffffu, bi * (wi - s), q);
+      if (lane == q) res = t;
+      if (lane > q && lane < nbp) s += gsh[lane * NB + q] * t;
+    }
+    if (lane < nbp) w2[lane] = res;
   }
   __syncthreads();
   for (int64_t i = j0 + tid; i < p; i += UT) {
@@ -248,8 +242,7 @@ __global__ void hqr_r_kernel(const double *A, int64_t p, int32_t m, const double
 }
 
 static size_t panel_smem(int per) {
-  return sizeof(double) * ((size_t)NB * (per | 1) + (size_t)MAXCS * (NB + 1) + (size_t)NB * NB + NB + 2 +
-                           (size_t)NB * NB + (size_t)PT);
+  return sizeof(double) * ((size_t)NB * (per | 1) + (size_t)MAXCS * (NB + 1) + (size_t)NB * NB + NB + 2 + (size_t)PT);
 }
 
 // Largest cluster (16, 8 or 4 CTAs) that fits the first panel of p rows.
