@@ -203,12 +203,32 @@ __global__ void __launch_bounds__(UT) hqr_update_kernel(Args a) {
   const int nbp = a.nbp;
   double *z = a.A + (int64_t)(j0 + nbp + blockIdx.x) * p;
   for (int e = tid; e < nbp * NB; e += UT) gsh[e] = a.Tp[e];
-  for (int k = warp; k < nbp; k += UT / 32) {
-    const double *v = a.S + (j0 + k) * a.lds;
-    double d = 0.0;
-    for (int64_t i = j0 + k + lane; i < p; i += 32) d += v[i] * z[i];
-    d = warp_sum(d);
-    if (lane == 0) w[k] = d;
+  // w_k = v_k . z: warp w takes k = w, w + 8, w + 16, w + 24 together (four
+  // independent FMA chains per lane, z read once for all four); V = S is zero
+  // above each reflector's diagonal, so every k starts at row j0
+  static_assert(UT / 32 * 4 == NB, "four reflectors per warp");
+  {
+    const int k0 = warp, k1 = warp + 8, k2 = warp + 16, k3 = warp + 24;
+    const double *v0 = a.S + (j0 + (k0 < nbp ? k0 : 0)) * a.lds, *v1 = a.S + (j0 + (k1 < nbp ? k1 : 0)) * a.lds;
+    const double *v2 = a.S + (j0 + (k2 < nbp ? k2 : 0)) * a.lds, *v3 = a.S + (j0 + (k3 < nbp ? k3 : 0)) * a.lds;
+    double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+    for (int64_t i = j0 + lane; i < p; i += 32) {
+      const double zi = z[i];
+      if (k0 < nbp) d0 += v0[i] * zi;
+      if (k1 < nbp) d1 += v1[i] * zi;
+      if (k2 < nbp) d2 += v2[i] * zi;
+      if (k3 < nbp) d3 += v3[i] * zi;
+    }
+    d0 = warp_sum(d0);
+    d1 = warp_sum(d1);
+    d2 = warp_sum(d2);
+    d3 = warp_sum(d3);
+    if (lane == 0) {
+      if (k0 < nbp) w[k0] = d0;
+      if (k1 < nbp) w[k1] = d1;
+      if (k2 < nbp) w[k2] = d2;
+      if (k3 < nbp) w[k3] = d3;
+    }
   }
   __syncthreads();
   if (warp == 0) {
@@ -224,11 +244,19 @@ __global__ void __launch_bounds__(UT) hqr_update_kernel(Args a) {
     if (lane < nbp) w2[lane] = res;
   }
   __syncthreads();
+  // z_i -= sum_k v_k(i) w2_k (zeros above the diagonals included), four chains
   for (int64_t i = j0 + tid; i < p; i += UT) {
-    double acc = 0.0;
-    const int kmax = (int)clamp64(i - j0 + 1, 0, nbp);
-    for (int k = 0; k < kmax; ++k) acc += a.S[(j0 + k) * a.lds + i] * w2[k];
-    z[i] -= acc;
+    const double *vi = a.S + j0 * a.lds + i;
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+    int k = 0;
+    for (; k + 3 < nbp; k += 4) {
+      c0 += vi[(int64_t)k * a.lds] * w2[k];
+      c1 += vi[(int64_t)(k + 1) * a.lds] * w2[k + 1];
+      c2 += vi[(int64_t)(k + 2) * a.lds] * w2[k + 2];
+      c3 += vi[(int64_t)(k + 3) * a.lds] * w2[k + 3];
+    }
+    for (; k < nbp; ++k) c0 += vi[(int64_t)k * a.lds] * w2[k];
+    z[i] -= (c0 + c1) + (c2 + c3);
   }
 }
 
