@@ -90,7 +90,8 @@ void rhqr_default_opts(rhqr_opts *opts /* host */);
 /*
  * rhqr_sketch_create -- draw the sketch Omega_full (k x n) from `seed`
  * (Section 2.3; the paper leaves the generator open, this library uses the
- * counter-based SplitMix64 scheme described in the design doc).
+ * counter-based SplitMix64 scheme: entry i of stream t is the SplitMix64 output
+ * function of seed * 0x9E3779B97F4A7C15 + t * 2^56 + i).
  *   kind = RHQR_SKETCH_SRHT: Omega_full = sqrt(N/k) P H D, N = 2^ceil(log2 n);
  *          stores N random signs and the k sampled rows (increasing).
  *   kind = RHQR_SKETCH_GAUSSIAN: Omega_full = G / sqrt(k), G i.i.d. N(0,1)
@@ -220,6 +221,25 @@ rhqr_status rhqr_arnoldi_step(rhqr_arnoldi a, const void *w, double *h, void *q_
                               rhqr_stream_t stream);
 rhqr_status rhqr_arnoldi_export(rhqr_arnoldi a, void *U, int64_t ldu, double *S, int64_t lds, double *T,
                                 int32_t *count, rhqr_stream_t stream);
+
+/*
+ * rhqr_arnoldi_solution -- the RHQR-GMRES update (Algorithm 8): after m steps
+ * (1 <= m <= steps taken since begin), y = argmin || h0 - H y ||_2, which is
+ * the sketched minimal-residual condition of eq. rgmresopti (Psi Q_{m+1} is
+ * orthonormal, so || Psi (b - A x) || = || h0 - H y || for x = x0 + Q_m y),
+ * and x = x0 + Q_m y with Q_m y = [y; 0] - U_m T_m S_m^t y (the compact form;
+ * rows 0..m-1 of S's first m columns, the identity top block of Psi).
+ *   H   : device float64, (m+1) x m (column j = the first m+1 entries of the
+ *         h returned by step j), column-major, ldh >= m+1; read only.
+ *   h0  : device float64, mmax+1 entries, as returned by begin.
+ *   x0  : device, n, basis dtype (the x0 of r0 = b - A x0); x: device, n,
+ *         basis dtype, may equal x0; x == NULL skips the update (y and res only).
+ *   y   : device float64, m entries (output); res: device float64, 1 (output).
+ * Float64 Givens rotations on the device; nothing is synchronised.  Returns
+ * RHQR_EINVAL when m exceeds the steps taken or ldh < m+1.
+ */
+rhqr_status rhqr_arnoldi_solution(rhqr_arnoldi a, const double *H, int64_t ldh, int32_t m, const double *h0,
+                                  const void *x0, void *x, double *y, double *res, rhqr_stream_t stream);
 
 /*
  * Batched recRHQR (Algorithm 6 with the refinement passes of rhqr_factor) of

@@ -4,7 +4,7 @@ Indices are 0-based: the paper's column j (1..m) is ``j-1`` here.  Matrices
 are numpy arrays; float64 arrays give the FP64 oracle, object arrays of
 ``decimal.Decimal`` give the same algorithm in extended precision (tests).
 
-Readings of passages that are ambiguous or garbled (each listed in the design doc):
+Readings of passages that are ambiguous or garbled:
 
 * sign(0) := +1 in RHVector (Algorithm 2 is silent).
 * Unit-diagonal scaling (Algorithm 2, second option) returns
@@ -13,13 +13,13 @@ Readings of passages that are ambiguous or garbled (each listed in the design doc):
   unflipped vector, which is the same quantity.  The norm scaling
   (||s|| = sqrt 2) divides by sqrt(rho (rho + |a|)), again the sign-correct form.
 * The T recurrence of Prop. "generalcompactwoodburry" uses beta_{j+1} in the new
-  column (as in the deterministic recurrence of Section 2.2 and line t_j of
+  column (as in the deterministic recurrence of Section 2.2 and in
   Algorithm 4); the printed beta_j is a typo.
 * Algorithm 6 writes ut(T^t Y^t Z) with Y = S_{1:m,1:m}, a dimension mismatch;
   the derivation in Section 3.3 uses the full S = Psi U, so M = ut(T^t S^t Z).
   Its "backward solve" of W_2 = X M runs forward over the columns (the explicit
   recursion of Section 3.3).
-* Algorithm 7 line "z <- RhSk(z)" is read as z <- RhSk(w) with w = A q_j.
+* The sketch step z <- RhSk(z) of Algorithm 7 is read as z <- RhSk(w) with w = A q_j.
 * RHQR-GMRES uses beta e_1 := h_0 = (-sigma_1 rho_1) e_1 from the first
   reflector (Algorithm 8's sign<b,e_1>||c|| ignores x_0).
 """

@@ -95,6 +95,7 @@ _SIGNATURES = {
     "rhqr_arnoldi_step": (_i32, [_p, _p, _p, _p, _p, _p]),
     "rhqr_arnoldi_export": (_i32, [_p, _p, _i64, _p, _i64, _p, ctypes.POINTER(_i32), _p]),
     "rhqr_sketch_apply_noalloc": (_i32, [_p, _i32, _p, _i32, _i64, _i32, _i64, _p, _i64, _p]),
+    "rhqr_arnoldi_solution": (_i32, [_p, _p, _i64, _i32, _p, _p, _p, _p, _p, _p]),
     "rhqr_batch_create": (_i32, [_i32, _p, _p, _i32, _p, _p, _p, ctypes.POINTER(rhqr_opts), _p, _p, _p, _p, _p, _p,
                                  ctypes.POINTER(_p)]),
     "rhqr_batch_workspace_size": (_i32, [_p, ctypes.POINTER(_sz)]),
@@ -279,6 +280,11 @@ def rhqr_arnoldi_export(a, U=None, ldu=0, S=None, lds=0, T=None, stream=None) ->
     _check("rhqr_arnoldi_export", load().rhqr_arnoldi_export(a, _ptr(U), ldu, _ptr(S), lds, _ptr(T),
                                                              ctypes.byref(cnt), _stream(stream)))
     return cnt.value
+
+
+def rhqr_arnoldi_solution(a, H, ldh, m, h0, x0, x, y, res, stream=None) -> None:
+    _check("rhqr_arnoldi_solution", load().rhqr_arnoldi_solution(a, _ptr(H), ldh, m, _ptr(h0), _ptr(x0), _ptr(x),
+                                                                 _ptr(y), _ptr(res), _stream(stream)))
 
 
 def rhqr_sketch_apply_noalloc(s, m, X, xt, n, c, ldx, Z, ldz, stream=None) -> None:

@@ -26,6 +26,7 @@ struct rhqr_sketch_s {
 struct rhqr_arnoldi_s {
   rhqr::ArnoldiState st;
   void *mem;
+  double *lsq;  // scratch of rhqr_arnoldi_solution (the Givens triangle, coefficients)
 };
 
 namespace rhqr {
@@ -558,6 +559,12 @@ rhqr_status rhqr_arnoldi_create(rhqr_sketch s, int64_t n, int32_t mmax, int32_t 
     delete a;
     return RHQR_ENOMEM;
   }
+  if (cudaMalloc((void **)&a->lsq, sizeof(double) * arnoldi_solution_scratch_doubles(M)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    cudaFree(a->mem);
+    delete a;
+    return RHQR_ENOMEM;
+  }
   *out = a;
   return RHQR_OK;
 }
@@ -565,8 +572,9 @@ rhqr_status rhqr_arnoldi_create(rhqr_sketch s, int64_t n, int32_t mmax, int32_t 
 rhqr_status rhqr_arnoldi_destroy(rhqr_arnoldi a) {
   if (a == nullptr) return RHQR_OK;
   cudaError_t e = cudaFree(a->mem);
+  cudaError_t e2 = cudaFree(a->lsq);
   delete a;
-  return e == cudaSuccess ? RHQR_OK : RHQR_ECUDA;
+  return (e == cudaSuccess && e2 == cudaSuccess) ? RHQR_OK : RHQR_ECUDA;
 }
 
 rhqr_status rhqr_arnoldi_begin(rhqr_arnoldi a, const void *r0, double *h0, void *q1, rhqr_info *info,
@@ -582,6 +590,13 @@ rhqr_status rhqr_arnoldi_step(rhqr_arnoldi a, const void *w, double *h, void *q_
   if (a == nullptr || w == nullptr || h == nullptr || info == nullptr) return RHQR_EINVAL;
   if (a->st.j < 1 || a->st.j >= a->st.M) return RHQR_EINVAL;
   return arnoldi_step(a->st, w, h, q_next, info, (cudaStream_t)stream);
+}
+
+rhqr_status rhqr_arnoldi_solution(rhqr_arnoldi a, const double *H, int64_t ldh, int32_t m, const double *h0,
+                                  const void *x0, void *x, double *y, double *res, rhqr_stream_t stream) {
+  if (a == nullptr || H == nullptr || h0 == nullptr || y == nullptr || res == nullptr) return RHQR_EINVAL;
+  if (x != nullptr && x0 == nullptr) return RHQR_EINVAL;
+  return arnoldi_solution(a->st, a->lsq, H, ldh, m, h0, x0, x, y, res, (cudaStream_t)stream);
 }
 
 rhqr_status rhqr_arnoldi_export(rhqr_arnoldi a, void *U, int64_t ldu, double *S, int64_t lds, double *T,

@@ -627,4 +627,128 @@ rhqr_status arnoldi_step(ArnoldiState &a, const void *w, double *h, void *qn, rh
   return arnoldi_step_t<float>(a, (const float *)w, h, (float *)qn, info, st);
 }
 
+// ---------------------------------------------------------------------------
+// RHQR-GMRES (Algorithm 8): the sketched minimal-residual solution
+// ---------------------------------------------------------------------------
+
+// y = argmin || h0 - H y || for the (m+1) x m Hessenberg H (eq. rgmresopti),
+// by Givens rotations in float64: thread 0 rotates column after column (the
+// column being rotated and the rotations live in shared memory, the triangle
+// R goes to `Rs`, ld = m), then the warp back-substitutes by columns (lane i
+// keeps the partial sum of row i).  res = || h0 - H y ||.
+__global__ void arnoldi_lsq_kernel(const double *H, int64_t ldh, int32_t m, int32_t M, const double *h0, double *Rs,
+                                   double *y, double *res) {
+  extern __shared__ double sh[];
+  double *col = sh;          // [m + 1]
+  double *cs = sh + m + 1;   // [m]
+  double *sn = cs + m;       // [m]
+  double *g = sn + m;        // [m + 1]
+  const int lane = threadIdx.x;
+  for (int i = lane; i <= m; i += 32) g[i] = h0[i];
+  __syncwarp();
+  if (lane == 0) {
+    for (int j = 0; j < m; ++j) {
+      for (int i = 0; i <= j + 1; ++i) col[i] = H[(int64_t)j * ldh + i];
+      for (int i = 0; i < j; ++i) {
+        const double a = col[i], b = col[i + 1];
+        col[i] = cs[i] * a + sn[i] * b;
+        col[i + 1] = cs[i] * b - sn[i] * a;
+      }
+      const double a = col[j], b = col[j + 1];
+      const double d = hypot(a, b);
+      const double c = d == 0.0 ? 1.0 : a / d, sv = d == 0.0 ? 0.0 : b / d;
+      cs[j] = c;
+      sn[j] = sv;
+      col[j] = d;
+      const double g0 = g[j], g1 = g[j + 1];
+      g[j] = c * g0 + sv * g1;
+      g[j + 1] = c * g1 - sv * g0;
+      for (int i = 0; i <= j; ++i) Rs[(int64_t)j * m + i] = col[i];
+    }
+    // entries of h0 below row m are not reached by H's first m columns
+    double tail = g[m] * g[m];
+    for (int i = m + 1; i < M; ++i) tail += h0[i] * h0[i];
+    *res = sqrt(tail);
+  }
+  __syncwarp();
+  __threadfence_block();
+  // back substitution R y = g[0:m], by columns: y_l = s_l / R_ll, then s_i -= R_il y_l
+  double sacc[32];
+#pragma unroll
+  for (int t = 0; t < 32; ++t) sacc[t] = 0.0;
+  for (int l = m - 1; l >= 0; --l) {
+    const int owner = l & 31, slot = l >> 5;
+    double yl = 0.0;
+    if (lane == owner) {
+      double sv = 0.0;
+#pragma unroll
+      for (int t = 0; t < 32; ++t)
+        if (t == slot) sv = sacc[t];
+      yl = (g[l] - sv) / Rs[(int64_t)l * m + l];
+      y[l] = yl;
+    }
+    yl = __shfl_sync(0xffffffffu, yl, owner);
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const int i = lane + 32 * t;
+      if (i < l) sacc[t] += Rs[(int64_t)l * m + i] * yl;
+    }
+  }
+}
+
+// coef = T_m (S_m^t y) with S_m = rows 0..m-1 of S's first m columns (the
+// identity top block of Psi keeps [y; 0] unchanged): v_i = sum_{j >= i} S_ji y_j,
+// coef_l = sum_{i >= l} T_li v_i
+__global__ void arnoldi_solution_coef_kernel(const double *T, int32_t M, const double *S, int64_t lds, int32_t m,
+                                             const double *y, double *v, double *coef) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double acc = 0.0;
+    for (int j = i; j < m; ++j) acc += S[(int64_t)i * lds + j] * y[j];
+    v[i] = acc;
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < m; l += blockDim.x) {
+    double acc = 0.0;
+    for (int i = l; i < m; ++i) acc += T[(int64_t)i * M + l] * v[i];
+    coef[l] = acc;
+  }
+}
+
+// x = x0 + [y; 0] - U_m coef (columns 0..m-1 of U are scaled once m steps were taken)
+template <class T>
+__global__ void arnoldi_x_kernel(const T *U, int64_t ldu, int64_t n, int32_t m, const double *coef,
+                                 const double *y, const T *x0, T *x) {
+  __shared__ double c_s[1024];
+  for (int l = threadIdx.x; l < m; l += blockDim.x) c_s[l] = coef[l];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = (double)x0[i] + (i < m ? y[i] : 0.0);
+  for (int l = 0; l < m; ++l) acc -= (double)U[(int64_t)l * ldu + i] * c_s[l];
+  x[i] = (T)acc;
+}
+
+size_t arnoldi_solution_scratch_doubles(int32_t M) { return (size_t)M * M + 2 * (size_t)M; }
+
+rhqr_status arnoldi_solution(const ArnoldiState &a, double *scratch, const double *H, int64_t ldh, int32_t m,
+                             const double *h0, const void *x0, void *x, double *y, double *res, cudaStream_t st) {
+  if (m < 1 || m > a.j - 1 || m > a.M - 1 || ldh < m + 1) return RHQR_EINVAL;
+  double *Rs = scratch, *v = scratch + (size_t)a.M * a.M, *coef = v + a.M;
+  const size_t smem = sizeof(double) * (4 * (size_t)m + 2);  // column, cosines, sines, rotated h0
+  arnoldi_lsq_kernel<<<1, 32, smem, st>>>(H, ldh, m, a.M, h0, Rs, y, res);
+  RHQR_LAUNCH_CHECK();
+  if (x == nullptr) return RHQR_OK;
+  arnoldi_solution_coef_kernel<<<1, 256, 0, st>>>(a.T, a.M, a.S, a.lds, m, y, v, coef);
+  RHQR_LAUNCH_CHECK();
+  const unsigned grid = (unsigned)ceil_div(a.n, (int64_t)256);
+  if (a.dtype == RHQR_F64)
+    arnoldi_x_kernel<double><<<grid, 256, 0, st>>>((const double *)a.U, a.ldu, a.n, m, coef, y, (const double *)x0,
+                                                   (double *)x);
+  else
+    arnoldi_x_kernel<float><<<grid, 256, 0, st>>>((const float *)a.U, a.ldu, a.n, m, coef, y, (const float *)x0,
+                                                  (float *)x);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
+}
+
 }  // namespace rhqr

@@ -34,5 +34,10 @@ rhqr_status arnoldi_carve(ArnoldiState &a, void *mem, size_t bytes);
 rhqr_status arnoldi_begin(ArnoldiState &a, const void *r0, double *h0, void *q1, rhqr_info *info, cudaStream_t st);
 rhqr_status arnoldi_scale_copy(const ArnoldiState &a, void *Udst, int64_t ldu, cudaStream_t st);
 rhqr_status arnoldi_step(ArnoldiState &a, const void *w, double *h, void *qn, rhqr_info *info, cudaStream_t st);
+// RHQR-GMRES solution (Algorithm 8): y = argmin ||h0 - H y|| (res = the minimum),
+// x = x0 + Q_m y when x != nullptr; scratch holds arnoldi_solution_scratch_doubles(M).
+size_t arnoldi_solution_scratch_doubles(int32_t M);
+rhqr_status arnoldi_solution(const ArnoldiState &a, double *scratch, const double *H, int64_t ldh, int32_t m,
+                             const double *h0, const void *x0, void *x, double *y, double *res, cudaStream_t st);
 
 }  // namespace rhqr

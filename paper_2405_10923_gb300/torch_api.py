@@ -13,11 +13,11 @@ from . import (ALG_LEFT, ALG_REC, BF16, F16, F32, F64, GAUSSIAN, SRHT, colmajor,
                rhqr_batch_create, rhqr_batch_destroy, rhqr_batch_get_tuning, rhqr_batch_set_tuning, rhqr_batch_tune,
                rhqr_batch_workspace_size, rhqr_factor_batched, rhqr_arnoldi_begin, rhqr_arnoldi_create, rhqr_arnoldi_destroy, rhqr_arnoldi_export, rhqr_arnoldi_step,
                rhqr_default_opts, rhqr_factor, rhqr_pipeline_create, rhqr_pipeline_destroy, rhqr_pipeline_submit,
-               rhqr_pipeline_wait, rhqr_reconstruct, rhqr_sketch_apply, rhqr_sketch_apply_workspace,
+               rhqr_pipeline_wait, rhqr_arnoldi_solution, rhqr_reconstruct, rhqr_sketch_apply, rhqr_sketch_apply_workspace,
                rhqr_sketch_create, rhqr_sketch_destroy, rhqr_sketch_export, rhqr_sketch_shape, rhqr_workspace_size)
 
 TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}
-__all__ = ["Sketch", "Arnoldi", "Batch", "Pipeline", "factor", "reconstruct", "colmajor", "ALG_LEFT", "ALG_REC", "GAUSSIAN", "SRHT"]
+__all__ = ["Sketch", "Arnoldi", "GMRES", "Batch", "Pipeline", "factor", "reconstruct", "colmajor", "ALG_LEFT", "ALG_REC", "GAUSSIAN", "SRHT"]
 
 
 class Sketch:
@@ -188,12 +188,64 @@ class Arnoldi:
         rhqr_arnoldi_step(self.handle, w, h, q, self.info)
         return h, q
 
+    def solution(self, H: torch.Tensor, m: int, h0: torch.Tensor, x0=None, x=None):
+        """rhqr_arnoldi_solution: y = argmin ||h0 - H[:m+1, :m] y|| and, when x0
+        is given, x = x0 + Q_m y (into x, default a new tensor).  H is the
+        column-major (mmax+1) x mmax float64 matrix of the step outputs."""
+        y = torch.zeros(max(m, 1), dtype=torch.float64, device=self.device)
+        res = torch.zeros(1, dtype=torch.float64, device=self.device)
+        if x0 is not None and x is None:
+            x = torch.empty_like(x0)
+        rhqr_arnoldi_solution(self.handle, H, ld_of(H), m, h0, x0, x, y, res)
+        return y[:m], res, x
+
     def export(self):
         U = colmajor(torch.zeros((self.n, self.M), dtype=self.dtype, device=self.device))
         S = colmajor(torch.zeros((self.k + self.M, self.M), dtype=torch.float64, device=self.device))
         T = torch.zeros((self.M, self.M), dtype=torch.float64, device=self.device)
         cnt = rhqr_arnoldi_export(self.handle, U, ld_of(U), S, ld_of(S), T)
         return U, S, T.t(), cnt
+
+
+class GMRES:
+    """Restarted RHQR-GMRES (Algorithm 8) over the library's Arnoldi steps with a
+    caller-applied operator A (a function of a device vector).  Each cycle takes
+    up to `restart` steps from r0 = b - A x, checks the sketched residual
+    ||h0 - H y|| (= ||Psi (b - A x)||) every `check` steps, and updates x by
+    rhqr_arnoldi_solution; it stops when the true residual ||b - A x|| <= tol ||b||."""
+
+    def __init__(self, sk: Sketch, n: int, restart: int, dtype=torch.float64, device="cuda"):
+        self.arn = Arnoldi(sk, n, restart, dtype=dtype, device=device)
+        self.restart, self.n, self.dtype, self.device = restart, n, dtype, device
+        self.H = colmajor(torch.zeros((restart + 1, restart), dtype=torch.float64, device=device))
+
+    def close(self):
+        self.arn.close()
+
+    def solve(self, A, b: torch.Tensor, x0=None, tol: float = 1e-8, max_cycles: int = 50, check: int = 10):
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        bnorm = float(torch.linalg.norm(b.double()))
+        history = []
+        for cycle in range(max_cycles):
+            r = b - A(x)
+            rnorm = float(torch.linalg.norm(r.double()))
+            history.append(rnorm / bnorm)
+            if rnorm <= tol * bnorm:
+                return x, history
+            h0, q = self.arn.begin(r)
+            steps = 0
+            for j in range(self.restart):
+                h, q = self.arn.step(A(q))
+                self.H[:, j] = h
+                steps = j + 1
+                if steps % check == 0 and steps < self.restart:
+                    _, res, _ = self.arn.solution(self.H, steps, h0)
+                    if float(res) <= 0.5 * tol * bnorm:
+                        break
+            _, _, x = self.arn.solution(self.H, steps, h0, x0=x, x=x)
+        r = b - A(x)
+        history.append(float(torch.linalg.norm(r.double())) / bnorm)
+        return x, history
 
 
 class Batch:

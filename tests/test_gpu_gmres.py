@@ -1,0 +1,76 @@
+"""RHQR-GMRES (Algorithm 8) on the GPU: the least-squares solution and the
+update x = x0 + Q_m y of rhqr_arnoldi_solution against the oracle's
+rhqr_gmres on the same sketch and operator, and a restarted solve of the
+2-D convection-diffusion system to 1e-8."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import rhqr_inputs as ri  # noqa: E402
+from oracle import rhqr, sketch  # noqa: E402
+
+
+@pytest.mark.parametrize("g,mmax,k", [(48, 30, 128), (40, 12, 64)])
+def test_arnoldi_solution_matches_oracle_gmres(gpu_lib, g, mmax, k):
+    from paper_2405_10923_gb300 import torch_api as ta
+
+    n = g * g
+    rng = np.random.default_rng(7)
+    b = rng.standard_normal(n)
+    x0 = 0.1 * rng.standard_normal(n)
+
+    def A_np(v):
+        return ri.stencil_apply(v.copy(), g)
+
+    osk = sketch.SRHTSketch(n, k, 77)
+    x_o, H_o, Q_o, h0_o = rhqr.rhqr_gmres(A_np, b, x0, osk, mmax)
+    y_o = np.linalg.lstsq(H_o, h0_o, rcond=None)[0]
+
+    sk = ta.Sketch(n, k, gpu_lib.SRHT, 77)
+    arn = ta.Arnoldi(sk, n, mmax, dtype=torch.float64)
+    bd = torch.tensor(b, device="cuda")
+    xd = torch.tensor(x0, device="cuda")
+    H = gpu_lib.colmajor(torch.zeros((mmax + 1, mmax), dtype=torch.float64, device="cuda"))
+    h0, q = arn.begin(bd - ri.stencil_apply(xd.clone(), g))
+    for j in range(mmax):
+        h, q = arn.step(ri.stencil_apply(q.clone(), g))
+        H[:, j] = h
+    y, res, x = arn.solution(H, mmax, h0, x0=xd)
+    torch.cuda.synchronize()
+    assert ta.read_info(arn.info)["status"] == 0
+    assert np.max(np.abs(H.cpu().numpy() - H_o)) <= 1e-10 * np.abs(H_o).max()
+    assert np.max(np.abs(y.cpu().numpy() - y_o)) <= 1e-9 * max(1.0, np.abs(y_o).max())
+    assert abs(float(res) - np.linalg.norm(h0_o - H_o @ y_o)) <= 1e-9 * np.linalg.norm(h0_o)
+    assert np.max(np.abs(x.cpu().numpy() - x_o)) <= 1e-10 * max(1.0, np.abs(x_o).max())
+    # sketched optimality (eq. rgmresopti): res is the sketched residual of x
+    r = b - A_np(x.cpu().numpy())
+    assert abs(np.linalg.norm(sketch.rh_sketch(r, mmax + 1, osk)) - float(res)) <= 1e-8 * np.linalg.norm(b)
+    # y only (no update), and fewer steps than taken
+    y2, res2, x2 = arn.solution(H, mmax - 3, h0)
+    y2_o = np.linalg.lstsq(H_o[: mmax - 2, : mmax - 3], h0_o[: mmax - 2], rcond=None)[0]
+    assert x2 is None
+    assert np.max(np.abs(y2.cpu().numpy() - y2_o)) <= 1e-9 * max(1.0, np.abs(y2_o).max())
+    with pytest.raises(gpu_lib.RHQRError):
+        arn.solution(H, mmax + 1, h0)
+    arn.close()
+    sk.close()
+
+
+def test_restarted_gmres_converges(gpu_lib):
+    from paper_2405_10923_gb300 import torch_api as ta
+
+    g = 32
+    n = g * g
+    sk = ta.Sketch(n, 128, gpu_lib.SRHT, 5)
+    b = torch.tensor(np.random.default_rng(3).standard_normal(n), device="cuda")
+    solver = ta.GMRES(sk, n, restart=60)
+    x, hist = solver.solve(lambda v: ri.stencil_apply(v.clone(), g), b, tol=1e-8, max_cycles=30)
+    r = b - ri.stencil_apply(x.clone(), g)
+    assert float(torch.linalg.norm(r) / torch.linalg.norm(b)) <= 1e-8, hist
+    assert hist[-1] < hist[0]
+    solver.close()
+    sk.close()
