@@ -12,8 +12,11 @@ warm-up, inputs resident on the device):
                 diffusion operator on a 1024 x 1024 grid (n = 2^20, Peclet 10),
                 SRHT k = 400, 100 steps, float64 and float32 basis; the operator
                 (torch, matrix-free) is timed with the step, as a user runs it
+  gmres       : restarted RHQR-GMRES (Algorithm 8) on the same system, restart
+                100, float64, up to --cycles cycles towards 1e-8 (time per cycle
+                and the relative residual after each)
 
-python -m paper_2405_10923_gb300.workloads_case [--cases left_small srht_left srht_rec arnoldi] [--reps 3]
+python -m paper_2405_10923_gb300.workloads_case [--cases left_small srht_left srht_rec arnoldi gmres] [--reps 3]
 
 Accuracy is reported with the library's own sketch of the result in float64
 (orth = max |eig(I - (Psi Q)^t Psi Q)|) and resid = ||W - QR||_F / ||W||_F
@@ -45,8 +48,9 @@ def _time(fn, reps):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--cases", nargs="+", default=["left_small", "srht_left", "srht_rec", "arnoldi"])
+    ap.add_argument("--cases", nargs="+", default=["left_small", "srht_left", "srht_rec", "arnoldi", "gmres"])
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--cycles", type=int, default=5)
     a = ap.parse_args()
 
     import numpy as np
@@ -128,6 +132,27 @@ def main():
                  ms_per_cycle=ms, us_per_step=ms * 1e3 / mmax, reflectors=cnt,
                  basis_gb=n * (mmax + 1) * b.element_size() / 1e9)
             arn.close()
+        sk.close()
+    if "gmres" in a.cases:
+        g = 1024
+        n, restart, k = g * g, 100, 400
+        sk = ta.Sketch(n, k, rh.SRHT, 2005)
+        b = torch.tensor(np.random.default_rng(1005).standard_normal(n), dtype=torch.float64, device="cuda")
+        solver = ta.GMRES(sk, n, restart)
+        A = lambda v: ri.stencil_apply(v.clone(), g)  # noqa: E731
+        solver.solve(A, b, tol=1e-8, max_cycles=1)  # warm-up
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        x, hist = solver.solve(A, b, tol=1e-8, max_cycles=a.cycles)
+        t1.record()
+        torch.cuda.synchronize()
+        cycles = len(hist) - 1
+        emit(case="gmres", path="restarted RHQR-GMRES f64", n=n, restart=restart, k=k, sketch="srht",
+             cycles=cycles, ms_per_cycle=t0.elapsed_time(t1) / max(cycles, 1),
+             relative_residuals=[float(f"{h:.3e}") for h in hist])
+        solver.close()
         sk.close()
 
 
