@@ -1,4 +1,4 @@
-// Host access to the driver's tensor-map encoder (for cp.async.bulk.tensor),
+// Host access to the CUDA driver API's tensor-map encoder (for cp.async.bulk.tensor),
 // looked up once through the runtime's driver entry point.
 #pragma once
 #include <cuda.h>
