@@ -147,6 +147,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time, returned on every rank (unchanged on one process)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, bytes_per_rank: int, ms: float) -> float:
+    """GB/s of W factored by `world` replicas that each factor bytes_per_rank in ms."""
+    return world * bytes_per_rank / (ms * 1e-3) / 1e9
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -244,13 +260,9 @@ def run_ours(a, rank: int, world: int, local_rank: int):
     rh.rhqr_profile_enable(False)
     clk = clocks.stop()
     barrier()
-    ms = e0.elapsed_time(e1) / a.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / a.steps, dist, dev)
     bytes_w = n * m * 4
-    value = world * bytes_w / (ms * 1e-3) / 1e9
+    value = replica_throughput(world, bytes_w, ms)
 
     # ---- accuracy of the mixed path (Psi Q accumulated in float64, same operator)
     def orth(skh, Q):
@@ -294,11 +306,7 @@ def run_ours(a, rank: int, world: int, local_rank: int):
     for i in range(e2e_steps):
         pipe.submit(Wh, Qh[i % 2], Rh[i % 2])
     pipe.wait()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps, dist, dev)
     e2e_ok = bool(torch.equal(Qh[(e2e_steps - 1) % 2], out["Q"].cpu()))
     pipe.close()
     del Wh, Qh, pipe
@@ -359,7 +367,7 @@ def run_ours(a, rank: int, world: int, local_rank: int):
         "accuracy": acc_mixed, "fp64_path": fp64, "speedup_vs_fp64_path": value / world / fp64["value"],
         "roofline": roof, "phases": phase_ms,
         "cpu_baseline": cpu_baseline(a),
-        "e2e": {"value": world * bytes_w / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": bytes_w,
+        "e2e": {"value": replica_throughput(world, bytes_w, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": bytes_w,
                 "d2h_bytes_per_step": bytes_w + m * m * 8, "steps": e2e_steps, "ms_per_step": e2e_ms,
                 "path": "rhqr_pipeline (host W in, host Q and R out; copies overlap neighbouring steps)",
                 "link_h2d_gbs": h2d_gbs, "link_d2h_gbs": d2h_gbs, "q_equals_device_path": e2e_ok},
