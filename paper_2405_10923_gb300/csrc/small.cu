@@ -125,8 +125,10 @@ __global__ void sts_upper_kernel(const double *S, int64_t lds, int64_t p, int32_
 //   T[j, j] = beta_j; T[i, j] = -beta_i sum_{l=i+1..j} SS[i, l] T[l, j], i = j-1..0,
 // as a backward column sweep over l (one warp per column).
 __global__ void t_from_woodbury_kernel(const double *SS, const double *beta, int32_t m, double *T) {
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (j >= m) return;
+  // one warp per column, the longest sweeps (largest j) first
+  const int jj = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (jj >= m) return;
+  const int j = m - 1 - jj;
   column_sweep<4>(SS, m, m, j, beta[j], beta, false, T + (int64_t)j * m);
 }
 
@@ -255,7 +257,7 @@ rhqr_status t_factor_small(const double *S, int64_t lds, int64_t p, int32_t m, c
   RHQR_CUDA_TRY(cudaMemsetAsync(SS, 0, sizeof(double) * m * m, st));
   sts_upper_kernel<<<m, 256, 0, st>>>(S, lds, p, m, SS);
   RHQR_LAUNCH_CHECK();
-  t_from_woodbury_kernel<<<(unsigned)ceil_div(m, 4), 128, 0, st>>>(SS, beta, m, T);
+  t_from_woodbury_kernel<<<(unsigned)m, 32, 0, st>>>(SS, beta, m, T);  // spread over the SMs (FP64 issue-bound)
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }

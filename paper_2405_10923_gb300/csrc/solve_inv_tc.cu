@@ -48,14 +48,16 @@ namespace rhqr {
 // column): once x_l is known, the partial sums s_i (i < l) take R_il x_l and
 // x_{l-1} = -s_{l-1} / R_{l-1,l-1}.
 __global__ void upper_inverse_kernel(const double *R, int32_t m, double *Rinv) {
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (j >= m) return;
+  // one warp per column, the longest sweeps (largest j) first
+  const int jj = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (jj >= m) return;
+  const int j = m - 1 - jj;
   column_sweep<4>(R, m, m, j, 1.0 / R[(int64_t)j * m + j], nullptr, true, Rinv + (int64_t)j * m);
 }
 
 rhqr_status upper_inverse(const double *R, int32_t m, double *Rinv, cudaStream_t st) {
   if (m < 1 || m > 256) return RHQR_ENOTSUP;
-  upper_inverse_kernel<<<(unsigned)ceil_div(m, 4), 128, 0, st>>>(R, m, Rinv);
+  upper_inverse_kernel<<<(unsigned)m, 32, 0, st>>>(R, m, Rinv);  // spread over the SMs (FP64 issue-bound)
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }
