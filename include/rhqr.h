@@ -96,7 +96,10 @@ void rhqr_default_opts(rhqr_opts *opts /* host */);
  *          stores N random signs and the k sampled rows (increasing).
  *   kind = RHQR_SKETCH_GAUSSIAN: Omega_full = G / sqrt(k), G i.i.d. N(0,1)
  *          (Box-Muller), materialised once in `omega_dtype` (F64, F32, BF16
- *          or F16) as a k x n row-major array (k*n elements of device memory).
+ *          or F16) as a k x n row-major array (k*n elements of device memory);
+ *          BF16 and F16 operators are stored a second time in the order the
+ *          tensor-core sketch reads them (256 x 64 tiles, k and n rounded up),
+ *          about twice the memory.
  * For a factorisation with m columns the sketch used is Psi_m = diag(I_m,
  * Omega) with Omega = columns m..n-1 of Omega_full (eq. psi).
  * Requires 1 <= k, k <= N (SRHT), n >= 2.  Allocates device memory (the only
