@@ -51,3 +51,5 @@ def test_argument_errors_are_synchronous():
     assert rh.load().rhqr_pipeline_submit(None, None, 0, None, 0, None, None, 0, None, None) == 1
     assert rh.load().rhqr_pipeline_wait(None) == 1
     assert rh.load().rhqr_pipeline_destroy(None) == 0
+    # GMRES solution: null handles and buffers are rejected on the host
+    assert rh.load().rhqr_arnoldi_solution(None, None, 0, 1, None, None, None, None, None, None) == 1
