@@ -313,3 +313,21 @@ def test_gmres_sketched_optimality_brute_force():
     Psi = sketch.psi_matrix(sk, mm + 1)
     c = np.linalg.lstsq(Psi @ A @ Kb, Psi @ r0, rcond=None)[0]
     assert np.max(np.abs(x - (x0 + Kb @ c))) < 1e-10 * np.abs(x).max()
+
+
+def test_panel_t_inverse_is_diag_inv_beta_plus_striu_gram():
+    """The blocked Householder QR never forms a panel's T: T^{-1} =
+    diag(1/beta) + striu(V^t V) (eq. generalwoodburry with Psi = I), and
+    T^t w is found by forward substitution with its transpose."""
+    rng = np.random.default_rng(21)
+    Z = rng.standard_normal((60, 12)) @ np.diag(np.logspace(0, -6, 12))
+    for scaling in ("unit", "norm"):
+        V, T, R = rhqr.householder_qr(Z, scaling)
+        beta = np.diag(T)
+        M = np.diag(1.0 / beta) + np.triu(V.T @ V, 1)
+        assert np.max(np.abs(np.linalg.inv(T) - M)) <= 1e-12 * np.abs(M).max()
+        w = rng.standard_normal(12)
+        w2 = np.zeros(12)
+        for q in range(12):  # forward substitution, M^t upper -> lower
+            w2[q] = beta[q] * (w[q] - M[:q, q] @ w2[:q])
+        assert np.max(np.abs(w2 - T.T @ w)) <= 1e-12 * np.abs(T.T @ w).max()
