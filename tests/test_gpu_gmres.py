@@ -74,3 +74,32 @@ def test_restarted_gmres_converges(gpu_lib):
     assert hist[-1] < hist[0]
     solver.close()
     sk.close()
+
+
+def test_arnoldi_solution_float32_basis(gpu_lib):
+    """float32 basis: the same sketched least-squares problem, x within float32
+    accuracy of the oracle's float64 cycle."""
+    from paper_2405_10923_gb300 import torch_api as ta
+
+    g, mmax, k = 40, 20, 64
+    n = g * g
+    rng = np.random.default_rng(9)
+    b = rng.standard_normal(n)
+    osk = sketch.SRHTSketch(n, k, 78)
+    x_o, H_o, _, h0_o = rhqr.rhqr_gmres(lambda v: ri.stencil_apply(v.copy(), g), b, np.zeros(n), osk, mmax)
+    sk = ta.Sketch(n, k, gpu_lib.SRHT, 78)
+    arn = ta.Arnoldi(sk, n, mmax, dtype=torch.float32)
+    bd = torch.tensor(b, dtype=torch.float32, device="cuda")
+    H = gpu_lib.colmajor(torch.zeros((mmax + 1, mmax), dtype=torch.float64, device="cuda"))
+    h0, q = arn.begin(bd)
+    for j in range(mmax):
+        h, q = arn.step(ri.stencil_apply(q.clone(), g))
+        H[:, j] = h
+    y, res, x = arn.solution(H, mmax, h0, x0=torch.zeros_like(bd))
+    torch.cuda.synchronize()
+    assert x.dtype == torch.float32
+    assert np.max(np.abs(x.double().cpu().numpy() - x_o)) <= 1e-4 * np.abs(x_o).max()
+    assert abs(float(res) - np.linalg.norm(h0_o - H_o @ np.linalg.lstsq(H_o, h0_o, rcond=None)[0])) \
+        <= 1e-4 * np.linalg.norm(h0_o)
+    arn.close()
+    sk.close()
