@@ -6,11 +6,13 @@
 //
 // Panels of 32 columns.  A panel is factored by one cluster of CTAs that hold
 // its rows in shared memory; each column costs two cluster barriers, and the
-// partial sums of the CTAs are read from each other's shared memory and added
-// in rank order, so the result does not depend on timing.  The panel's
-// reflectors are then applied to the trailing columns in compact form,
-// Z_t <- (I - V T^t V^t) Z_t with T upper triangular (T_jj = beta_j,
-// T_{0:j,j} = -beta_j T_{0:j,0:j} V_{:,0:j}^t v_j), one CTA per trailing column.
+// partial sums of the CTAs are pushed into each other's shared memory and
+// added in a fixed order, so the result does not depend on timing.  The
+// panel's reflectors are then applied to the trailing columns in compact form,
+// Z_t <- (I - V T^t V^t) Z_t, one CTA per trailing column.  T (upper
+// triangular, T_jj = beta_j) is never formed: T^{-1} = diag(1/beta) +
+// striu(V^t V), the panel collects V^t V with its own dot products, and the
+// update finds T^t (V^t z) by forward substitution with T^{-t}.
 #include <algorithm>
 
 #include "common.cuh"
