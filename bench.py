@@ -8,9 +8,10 @@ products on tcgen05 tensor cores (float32 data split into bf16 limbs), small
 Householder QR / T / R work in float64.  One step = one rhqr_factor call
 (all passes) on device-resident data; W (4.3 GB) is larger than L2, so no
 flush is needed.  Beside it: the plain FP64 GPU path on the same matrix, the
-accuracy of both against the stated tolerances, an end-to-end number with
-pinned host copies inside the timed region, and the FP64 CPU oracle timed on
-a bounded sample on the host cores.
+accuracy of both against the stated tolerances, an end-to-end number through
+the library's host pipeline (every step copies W in from page-locked host memory
+and Q, R back out; the copies of neighbouring steps overlap the factorisation),
+and the FP64 CPU oracle timed on a bounded sample on the host cores.
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Multi-GPU (torchrun): every rank factors its own matrix (independent
