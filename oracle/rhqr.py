@@ -173,6 +173,49 @@ def rhqr_left(W, sk, scaling: str = "unit"):
     return U, S, T, R
 
 
+def block_rhqr(W, sk, bs: int, scaling: str = "unit"):
+    """Algorithm 5 (blockRHQR): the columns of W in blocks of `bs`; block j is
+    first refreshed with the reflectors of every earlier block, one block at a
+    time (W^(j) <- W^(j) - U^(k) T^(k)t S^(k)t Psi W^(j), k < j: the printed
+    inner loop writes U^(j) where the earlier block U^(k) is meant), its rows
+    above the block give R's off-diagonal block, and Algorithm 4 factors it with
+    the global Psi = diag(I_m, Omega) and the global column indices.  Returns R
+    and the list of (first column, U^(j), S^(j), T^(j)).  In exact arithmetic
+    the reflectors are those of Algorithm 4 on the whole W and T^(j) is the
+    diagonal block of its T."""
+    W = np.asarray(W)
+    n, m = W.shape
+    R = _zeros((m, m), W)
+    blocks = []
+    for c0 in range(0, m, bs):
+        c1 = min(m, c0 + bs)
+        Wj = W[:, c0:c1].copy()
+        for _, Uk, Sk, Tk in blocks:
+            Y = rh_sketch(Wj, m, sk)
+            Wj = Wj - Uk @ (Tk.T @ (Sk.T @ Y))
+        R[:c0, c0:c1] = Wj[:c0]
+        b = c1 - c0
+        U = _zeros((n, b), W)
+        S = _zeros((sk.k + m, b), W)
+        T = _zeros((b, b), W)
+        for i in range(b):
+            j = c0 + i  # global column
+            w = Wj[:, i].copy()
+            if i >= 1:
+                y = rh_sketch(w, m, sk)
+                c = T[:i, :i].T @ (S[:, :i].T @ y)
+                w = w - U[:, :i] @ c
+            y = rh_sketch(w, m, sk)
+            u, sv, sigma, rho, beta = rh_vector(w, y, j, scaling)
+            R[c0:j, j] = w[c0:j]
+            R[j, j] = -sigma * rho
+            T[:, i] = t_column(T, S, sv, beta, i)
+            U[:, i] = u
+            S[:, i] = sv
+        blocks.append((c0, U, S, T))
+    return R, blocks
+
+
 def form_q(U, T, m: int | None = None):
     """Thin Q factor Q = [I_m; 0] - U T U_{1:m,1:m}^t (Section 3.2)."""
     n, mm = U.shape

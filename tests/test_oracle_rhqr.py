@@ -331,3 +331,44 @@ def test_panel_t_inverse_is_diag_inv_beta_plus_striu_gram():
         for q in range(12):  # forward substitution, M^t upper -> lower
             w2[q] = beta[q] * (w[q] - M[:q, q] @ w2[:q])
         assert np.max(np.abs(w2 - T.T @ w)) <= 1e-12 * np.abs(T.T @ w).max()
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 5 (blockRHQR)
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("kind,bs", [("gaussian", 4), ("srht", 3), ("srht", 12)])
+def test_block_rhqr_equals_left_looking(kind, bs):
+    W, sk = _case(kind, 300, 12, 40, 31)
+    U, S, T, R = rhqr.rhqr_left(W, sk)
+    RB, blocks = rhqr.block_rhqr(W, sk, bs)
+    scale = np.abs(R).max()
+    assert np.max(np.abs(RB - R)) <= 1e-12 * scale
+    for c0, Ub, Sb, Tb in blocks:
+        b = Ub.shape[1]
+        assert np.max(np.abs(Ub - U[:, c0:c0 + b])) <= 1e-11
+        assert np.max(np.abs(Sb - S[:, c0:c0 + b])) <= 1e-11
+        assert np.max(np.abs(Tb - T[c0:c0 + b, c0:c0 + b])) <= 1e-11
+    # W = prod_j (I - U^(j) T^(j) S^(j)t Psi) [R; 0]
+    Psi = sketch.psi_matrix(sk, W.shape[1])
+    P = np.eye(W.shape[0])
+    for _, Ub, Sb, Tb in blocks:
+        P = P @ (np.eye(W.shape[0]) - Ub @ Tb @ Sb.T @ Psi)
+    RW = np.zeros_like(W)
+    RW[: W.shape[1]] = RB
+    assert np.max(np.abs(P @ RW - W)) <= 1e-12 * np.abs(W).max()
+
+
+def test_block_rhqr_exact_arithmetic():
+    decimal.getcontext().prec = 60
+    r = np.random.default_rng(32)
+    n, m, k = 10, 4, 6
+    W = dec(r.integers(-5, 6, (n, m)))
+    sk = sketch.ExplicitSketch(dec(r.integers(-2, 3, (k, n))))
+    U, S, T, R = rhqr.rhqr_left(W, sk)
+    RB, blocks = rhqr.block_rhqr(W, sk, 2)
+    assert max(abs(v) for v in (RB - R).ravel()) < D("1e-50")
+    for c0, Ub, _, Tb in blocks:
+        assert max(abs(v) for v in (Ub - U[:, c0:c0 + 2]).ravel()) < D("1e-50")
+        assert max(abs(v) for v in (Tb - T[c0:c0 + 2, c0:c0 + 2]).ravel()) < D("1e-50")
