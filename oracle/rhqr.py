@@ -216,6 +216,62 @@ def block_rhqr(W, sk, bs: int, scaling: str = "unit"):
     return R, blocks
 
 
+def rgs(W, Omega):
+    """Randomized Gram-Schmidt with a given Omega (k x n): r = (Omega Q)^t Omega w_j
+    (the sketched least-squares coefficients, Omega Q having orthonormal
+    columns), q~ = w_j - Q r, R_jj = ||Omega q~||, q_j = q~ / R_jj.  The
+    reference that BLAS2-RGS (Section 6) equals in exact arithmetic."""
+    W = np.asarray(W)
+    n, m = W.shape
+    Q = _zeros((n, m), W)
+    R = _zeros((m, m), W)
+    SQ = _zeros((Omega.shape[0], m), W)  # Omega Q
+    for j in range(m):
+        w = W[:, j].copy()
+        if j:
+            r = SQ[:, :j].T @ (Omega @ w)
+            w = w - Q[:, :j] @ r
+            R[:j, j] = r
+        z = Omega @ w
+        rho = _sqrt(z @ z)
+        R[j, j] = rho
+        Q[:, j] = w / rho
+        SQ[:, j] = z / rho
+    return Q, R
+
+
+def blas2_rgs(W, Omega):
+    """Algorithm 9 (BLAS2-RGS): RHQR of [0_m; W] written on W (Section 6).
+    Column j: z = Omega w_j, r = T_{j-1}^t S_{j-1}^t z, w = w_j - Q_{j-1} r,
+    z = Omega w, rho = ||z||, q_j = w / rho, s_j = z / rho, R[:j, j] = r,
+    R_jj = rho, T[:j, j] = -T_{j-1} S_{j-1}^t s_j, T_jj = 1.  (The printed
+    rho = ||Omega z|| and s_j = rho^{-1} s are read as ||z|| and z / rho, as
+    the derivation before it gives.)  Returns Q, R, S = Omega Q and T, which
+    equals I in exact arithmetic and records the loss of sketched
+    orthogonality in floating point."""
+    W = np.asarray(W)
+    n, m = W.shape
+    Q = _zeros((n, m), W)
+    R = _zeros((m, m), W)
+    S = _zeros((Omega.shape[0], m), W)
+    T = _zeros((m, m), W)
+    for j in range(m):
+        w = W[:, j].copy()
+        if j:
+            r = T[:j, :j].T @ (S[:, :j].T @ (Omega @ w))
+            w = w - Q[:, :j] @ r
+            R[:j, j] = r
+        z = Omega @ w
+        rho = _sqrt(z @ z)
+        R[j, j] = rho
+        Q[:, j] = w / rho
+        S[:, j] = z / rho
+        if j:
+            T[:j, j] = -(T[:j, :j] @ (S[:, :j].T @ S[:, j]))
+        T[j, j] = _one(T)
+    return Q, R, S, T
+
+
 def form_q(U, T, m: int | None = None):
     """Thin Q factor Q = [I_m; 0] - U T U_{1:m,1:m}^t (Section 3.2)."""
     n, mm = U.shape

@@ -372,3 +372,43 @@ def test_block_rhqr_exact_arithmetic():
     for c0, Ub, _, Tb in blocks:
         assert max(abs(v) for v in (Ub - U[:, c0:c0 + 2]).ravel()) < D("1e-50")
         assert max(abs(v) for v in (Tb - T[c0:c0 + 2, c0:c0 + 2]).ravel()) < D("1e-50")
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 9 (BLAS2-RGS)
+# ---------------------------------------------------------------------------
+
+
+def test_blas2_rgs_equals_rgs_and_t_is_identity_in_exact_arithmetic():
+    decimal.getcontext().prec = 60
+    r = np.random.default_rng(41)
+    n, m, k = 12, 4, 7
+    W = dec(r.integers(-5, 6, (n, m)))
+    Om = dec(r.integers(-2, 3, (k, n)))
+    Q, R, S, T = rhqr.blas2_rgs(W, Om)
+    Qr, Rr = rhqr.rgs(W, Om)
+    assert max(abs(v) for v in (Q - Qr).ravel()) < D("1e-50")
+    assert max(abs(v) for v in (R - Rr).ravel()) < D("1e-50")
+    eye = np.eye(m, dtype=np.int64).astype(object)
+    assert max(abs(v) for v in (T - eye).ravel()) < D("1e-50")
+    assert max(abs(v) for v in (W - Q @ R).ravel()) < D("1e-50")
+    assert max(abs(v) for v in (S.T @ S - eye).ravel()) < D("1e-50")
+
+
+def test_blas2_rgs_is_rhqr_of_zero_topped_matrix():
+    """Section 6: RHQR of [0_m; W] with Psi = diag(I_m, Omega) gives u_j =
+    [e_j; -q_j]: the same Q and R as BLAS2-RGS (up to the column signs of the
+    reflector convention) and the same T."""
+    n, m, k = 400, 8, 40
+    W = ri.gaussian(n, m, 42)
+    Om = np.random.default_rng(43).standard_normal((k, n)) / math.sqrt(k)
+    Q, R, S, T = rhqr.blas2_rgs(W, Om)
+    Wbar = np.concatenate([np.zeros((m, m)), W])
+    skbar = sketch.ExplicitSketch(np.concatenate([np.zeros((k, m)), Om], axis=1))
+    U, Sh, Th, Rh = rhqr.rhqr_left(Wbar, skbar)
+    Qh = rhqr.form_q(U, Th)  # thin Q of [0; W]
+    d = np.sign(np.diag(Rh)) * np.sign(np.diag(R))
+    assert np.max(np.abs(Qh[:m])) <= 1e-13
+    assert np.max(np.abs(Qh[m:] * d - Q)) <= 1e-12
+    assert np.max(np.abs(d[:, None] * Rh - R)) <= 1e-12 * np.abs(R).max()
+    assert np.max(np.abs(Th - T)) <= 1e-11
