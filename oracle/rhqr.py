@@ -216,6 +216,60 @@ def block_rhqr(W, sk, bs: int, scaling: str = "unit"):
     return R, blocks
 
 
+def trim_rhqr_right(W, Omega, scaling: str = "unit"):
+    """Right-looking trimRHQR (Section 7, Algorithms 10-11) with the reflectors
+    H(u_j, Omega, j) = I - beta u_j (Omega u_j)^t [0 Omega_{j:n}] of eq. rhousebisbis.
+    Omega (l x n) must have unit first m columns.  Column j: w' = (0_j; w_{j:}),
+    rho = ||Omega w'||, sigma = sign(w_j) (sign(0) = +1), v = w' + sigma rho e_j,
+    s = Omega v, then either u = v / v_j (unit diagonal, beta = 2/||s||^2) or
+    u = sqrt(2) v / ||s|| (beta = 1); r_{0:j} = w_{0:j}, r_jj = -sigma rho; the
+    trailing columns get H(u, Omega, j).  (Readings: the scale alpha is the
+    reciprocal of v's first entry, as for Algorithm 2, rather than "the first
+    entry of v'", and the trailing update runs for every j, not only j >= 2.)
+    Returns U, S = Omega U, beta, R with W = H_1 ... H_m [R; 0]."""
+    W = np.array(W, copy=True)
+    n, m = W.shape
+    U = _zeros((n, m), W)
+    S = _zeros((Omega.shape[0], m), W)
+    R = _zeros((m, m), W)
+    beta = _zeros((m,), W)
+    for j in range(m):
+        w = W[:, j].copy()
+        wp = w.copy()
+        wp[:j] = 0 * wp[:j]
+        z = Omega @ wp
+        rho = _sqrt(z @ z)
+        if rho == 0:
+            raise Breakdown(j)
+        sigma = -1 if w[j] < 0 else 1
+        v = wp.copy()
+        v[j] = v[j] + sigma * rho
+        sv = Omega @ v
+        if scaling == "unit":
+            g = v[j]
+            u, sv = v / g, sv / g
+            b = 2 / (sv @ sv)
+        else:
+            a = _sqrt(2 * _one(W)) / _sqrt(sv @ sv)
+            u, sv = v * a, sv * a
+            b = _one(W)
+        R[:j, j] = w[:j]
+        R[j, j] = -sigma * rho
+        if j < m - 1:
+            X = Omega[:, j:] @ W[j:, j + 1:]
+            W[:, j + 1:] = W[:, j + 1:] - b * np.outer(u, sv @ X)
+        U[:, j], S[:, j], beta[j] = u, sv, b
+    return U, S, beta, R
+
+
+def trim_reflector(u, Omega, j: int, beta):
+    """Explicit H(u, Omega, j) = I - beta u (Omega u)^t [0_{l x j} Omega_{j:n}] (small n only)."""
+    n = u.shape[0]
+    Om = Omega.copy()
+    Om[:, :j] = 0 * Om[:, :j]
+    return np.eye(n) - beta * np.outer(u, (Omega @ u) @ Om)
+
+
 def rgs(W, Omega):
     """Randomized Gram-Schmidt with a given Omega (k x n): r = (Omega Q)^t Omega w_j
     (the sketched least-squares coefficients, Omega Q having orthonormal

@@ -412,3 +412,50 @@ def test_blas2_rgs_is_rhqr_of_zero_topped_matrix():
     assert np.max(np.abs(Qh[m:] * d - Q)) <= 1e-12
     assert np.max(np.abs(d[:, None] * Rh - R)) <= 1e-12 * np.abs(R).max()
     assert np.max(np.abs(Th - T)) <= 1e-11
+
+
+# ---------------------------------------------------------------------------
+# trimRHQR (Section 7), right-looking
+# ---------------------------------------------------------------------------
+
+
+def _unit_first_columns(Om, m):
+    Om = Om.copy()
+    Om[:, :m] = Om[:, :m] / np.linalg.norm(Om[:, :m], axis=0)
+    return Om
+
+
+@pytest.mark.parametrize("scaling", ["unit", "norm"])
+@pytest.mark.parametrize("k", [4, 12])  # fewer sampled rows than columns is allowed
+def test_trim_rhqr_factorisation_and_elimination(scaling, k):
+    n, m = 40, 6
+    rng = np.random.default_rng(51)
+    W = rng.standard_normal((n, m))
+    Om = _unit_first_columns(rng.standard_normal((k, n)) / math.sqrt(k), m)
+    U, S, beta, R = rhqr.trim_rhqr_right(W, Om, scaling)
+    assert np.max(np.abs(S - Om @ U)) <= 1e-13
+    assert np.allclose(np.tril(R, -1), 0)
+    H = [rhqr.trim_reflector(U[:, j], Om, j, beta[j]) for j in range(m)]
+    # the proposition: H_j leaves the first j entries and eliminates below j
+    A = W.copy()
+    for j in range(m):
+        A = H[j] @ A
+        assert np.max(np.abs(A[j + 1:, j])) <= 1e-12 * np.abs(W).max()
+    # eq. trimrhqrfact: H_m ... H_1 W = [R; 0] and W = H_1 ... H_m [R; 0]
+    assert np.max(np.abs(A[:m] - R)) <= 1e-12 * np.abs(R).max()
+    P = np.eye(n)
+    for j in range(m):
+        P = P @ H[j]
+    RW = np.zeros((n, m))
+    RW[:m] = R
+    assert np.max(np.abs(P @ RW - W)) <= 1e-12 * np.abs(W).max()
+    # each H_j is sketch-isometric for Psi_j = diag(I_j, Omega_{j:n}) and an involution
+    for j in range(m):
+        Psi = np.zeros((j + k, n))
+        Psi[:j, :j] = np.eye(j)
+        Psi[j:, j:] = Om[:, j:]
+        x = rng.standard_normal(n)
+        assert abs(np.linalg.norm(Psi @ H[j] @ x) - np.linalg.norm(Psi @ x)) <= 1e-12 * np.linalg.norm(x)
+        assert np.max(np.abs(H[j] @ H[j] - np.eye(n))) <= 1e-12
+    # the diagonal of R: -sigma ||Omega w'|| at each step (unit-column Omega makes |r_jj| positive)
+    assert np.all(np.abs(np.diag(R)) > 0)
