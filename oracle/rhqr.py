@@ -262,6 +262,64 @@ def trim_rhqr_right(W, Omega, scaling: str = "unit"):
     return U, S, beta, R
 
 
+def trim_ut(S, Omega, x):
+    """ut((Omega U)^t Omega) x: entry i is s_i . (Omega_{i:n} x_{i:n}) (row i of the
+    product with the columns before i removed), S = Omega U."""
+    out = _zeros((S.shape[1],) + x.shape[1:], x)
+    for i in range(S.shape[1]):
+        out[i] = S[:, i] @ (Omega[:, i:] @ x[i:])
+    return out
+
+
+def trim_rhqr_left(W, Omega, scaling: str = "unit"):
+    """Left-looking trimRHQR (Section 7): column j is refreshed with the earlier
+    reflectors through the compact left-wise form H_{j-1} ... H_1 = I - U Tt^t
+    ut((Omega U)^t Omega) (eq. trimrhqrcompactfact), then trimRHVector gives u_j.
+    T (right-wise compositions, the recurrence of eq. Tqdefbis) and Tt (left-wise,
+    eq. Sqdefbis) take t_{0:j,j} = -beta_j T_{0:j,0:j} S_{0:j}^t s_j and
+    tt_{0:j,j} = -beta_j Tt_{0:j,0:j} ([0 Omega_{j:n}] U_{0:j})^t s_j, diagonals beta_j.
+    Returns U, S = Omega U, T, Tt, R (eq. trimrhqr_finalform)."""
+    W = np.asarray(W)
+    n, m = W.shape
+    U = _zeros((n, m), W)
+    S = _zeros((Omega.shape[0], m), W)
+    T = _zeros((m, m), W)
+    Tt = _zeros((m, m), W)
+    R = _zeros((m, m), W)
+    for j in range(m):
+        w = W[:, j].copy()
+        if j:
+            w = w - U[:, :j] @ (Tt[:j, :j].T @ trim_ut(S[:, :j], Omega, w))
+        wp = w.copy()
+        wp[:j] = 0 * wp[:j]
+        z = Omega @ wp
+        rho = _sqrt(z @ z)
+        if rho == 0:
+            raise Breakdown(j)
+        sigma = -1 if w[j] < 0 else 1
+        v = wp.copy()
+        v[j] = v[j] + sigma * rho
+        sv = Omega @ v
+        if scaling == "unit":
+            g = v[j]
+            u, sv = v / g, sv / g
+            b = 2 / (sv @ sv)
+        else:
+            a = _sqrt(2 * _one(W)) / _sqrt(sv @ sv)
+            u, sv = v * a, sv * a
+            b = _one(W)
+        R[:j, j] = w[:j]
+        R[j, j] = -sigma * rho
+        if j:
+            T[:j, j] = -b * (T[:j, :j] @ (S[:, :j].T @ sv))
+            OU = Omega[:, j:] @ U[j:, :j]  # [0 Omega_{j:n}] U_{0:j}
+            Tt[:j, j] = -b * (Tt[:j, :j] @ (OU.T @ sv))
+        T[j, j] = b
+        Tt[j, j] = b
+        U[:, j], S[:, j] = u, sv
+    return U, S, T, Tt, R
+
+
 def trim_reflector(u, Omega, j: int, beta):
     """Explicit H(u, Omega, j) = I - beta u (Omega u)^t [0_{l x j} Omega_{j:n}] (small n only)."""
     n = u.shape[0]

@@ -459,3 +459,34 @@ def test_trim_rhqr_factorisation_and_elimination(scaling, k):
         assert np.max(np.abs(H[j] @ H[j] - np.eye(n))) <= 1e-12
     # the diagonal of R: -sigma ||Omega w'|| at each step (unit-column Omega makes |r_jj| positive)
     assert np.all(np.abs(np.diag(R)) > 0)
+
+
+@pytest.mark.parametrize("scaling", ["unit", "norm"])
+def test_trim_rhqr_left_equals_right_and_compact_forms(scaling):
+    n, m, k = 40, 6, 5  # fewer sampled rows than columns
+    rng = np.random.default_rng(52)
+    W = rng.standard_normal((n, m))
+    Om = _unit_first_columns(rng.standard_normal((k, n)) / math.sqrt(k), m)
+    Ur, Sr, br, Rr = rhqr.trim_rhqr_right(W, Om, scaling)
+    U, S, T, Tt, R = rhqr.trim_rhqr_left(W, Om, scaling)
+    assert np.max(np.abs(U - Ur)) <= 1e-12 and np.max(np.abs(S - Sr)) <= 1e-12
+    assert np.max(np.abs(R - Rr)) <= 1e-12 * np.abs(R).max()
+    # ut((Omega U)^t Omega) as a matrix, and the explicit reflectors
+    L = np.stack([rhqr.trim_ut(S, Om, e) for e in np.eye(n)], axis=1)
+    H = [rhqr.trim_reflector(U[:, j], Om, j, np.diag(T)[j]) for j in range(m)]
+    right = np.eye(n)
+    left = np.eye(n)
+    for j in range(m):
+        right = right @ H[j]
+        left = H[j] @ left
+    assert np.max(np.abs(right - (np.eye(n) - U @ T @ L))) <= 1e-12  # eq. compactrightbis
+    assert np.max(np.abs(left - (np.eye(n) - U @ Tt.T @ L))) <= 1e-12  # eq. trimrhqrcompactfact
+    # Woodbury forms (props woodburrybis and deltawoodburry)
+    Ti = np.linalg.inv(T)
+    assert np.max(np.abs(Ti + Ti.T - S.T @ S)) <= 1e-11
+    assert np.max(np.abs(Tt.T + np.linalg.inv(Ti - L @ U))) <= 1e-10 * np.abs(Tt).max()
+    # eq. trimrhqr_finalform
+    RW = np.zeros((n, m))
+    RW[:m] = R
+    assert np.max(np.abs((np.eye(n) - U @ T @ L) @ RW - W)) <= 1e-12 * np.abs(W).max()
+    assert np.max(np.abs((np.eye(n) - U @ Tt.T @ L) @ W - RW)) <= 1e-12 * np.abs(W).max()
