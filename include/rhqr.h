@@ -291,6 +291,27 @@ rhqr_status rhqr_batch_get_tuning(rhqr_batch b, int32_t *choice /* host, 3 */);
 rhqr_status rhqr_batch_set_tuning(rhqr_batch b, const int32_t *choice /* host, 3 */);
 
 /*
+ * rhqr_blas2_rgs -- BLAS2-RGS (Algorithm 9, Section 6): the randomized
+ * Householder QR of [0_m; W] written on W (n x m, dtype wt = F64 or F32, ldw),
+ * with Omega = Omega_full of the sketch (k x n, no exact top block).  In exact
+ * arithmetic it is randomized Gram-Schmidt: W = Q R with Omega Q orthonormal,
+ * and T = I; in floating point T records the loss of sketched orthogonality.
+ * Column j: z = Omega w_j, r = T^t S^t z, w = w_j - Q r, z = Omega w,
+ * rho = ||z||, q_j = w / rho, s_j = z / rho, R[0:j, j] = r, R_jj = rho,
+ * T[0:j, j] = -T S^t s_j, T_jj = 1.
+ *   Q : n x m, dtype wt, ldq >= n (output);  R, T : m x m float64 (ld = m);
+ *   S : k x m float64 (ld = k) = Omega Q;  info : device rhqr_info (a zero or
+ *   non-finite rho is reported with its column).
+ * ws/ws_bytes : device workspace of at least rhqr_blas2_rgs_workspace bytes.
+ * Requires 1 <= m <= 1024, n > m, and for the Gaussian kind n equal to the
+ * sketch's n.
+ */
+rhqr_status rhqr_blas2_rgs_workspace(rhqr_sketch s, int32_t wt, int64_t n, int32_t m, size_t *bytes);
+rhqr_status rhqr_blas2_rgs(rhqr_sketch s, const void *W, int32_t wt, int64_t n, int32_t m, int64_t ldw, void *Q,
+                           int64_t ldq, double *R, double *T, double *S, void *ws, size_t ws_bytes, rhqr_info *info,
+                           rhqr_stream_t stream);
+
+/*
  * Factorisation stream for matrices held in host memory (no counterpart in the
  * paper, which factors a matrix where the arithmetic runs).  Each submission
  * is one rhqr_factor (Algorithm 4 or 6, options as bound at create) of a host

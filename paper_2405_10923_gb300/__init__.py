@@ -96,6 +96,8 @@ _SIGNATURES = {
     "rhqr_arnoldi_export": (_i32, [_p, _p, _i64, _p, _i64, _p, ctypes.POINTER(_i32), _p]),
     "rhqr_sketch_apply_noalloc": (_i32, [_p, _i32, _p, _i32, _i64, _i32, _i64, _p, _i64, _p]),
     "rhqr_arnoldi_solution": (_i32, [_p, _p, _i64, _i32, _p, _p, _p, _p, _p, _p]),
+    "rhqr_blas2_rgs_workspace": (_i32, [_p, _i32, _i64, _i32, ctypes.POINTER(_sz)]),
+    "rhqr_blas2_rgs": (_i32, [_p, _p, _i32, _i64, _i32, _i64, _p, _i64, _p, _p, _p, _p, _sz, _p, _p]),
     "rhqr_batch_create": (_i32, [_i32, _p, _p, _i32, _p, _p, _p, ctypes.POINTER(rhqr_opts), _p, _p, _p, _p, _p, _p,
                                  ctypes.POINTER(_p)]),
     "rhqr_batch_workspace_size": (_i32, [_p, ctypes.POINTER(_sz)]),
@@ -285,6 +287,17 @@ def rhqr_arnoldi_export(a, U=None, ldu=0, S=None, lds=0, T=None, stream=None) ->
 def rhqr_arnoldi_solution(a, H, ldh, m, h0, x0, x, y, res, stream=None) -> None:
     _check("rhqr_arnoldi_solution", load().rhqr_arnoldi_solution(a, _ptr(H), ldh, m, _ptr(h0), _ptr(x0), _ptr(x),
                                                                  _ptr(y), _ptr(res), _stream(stream)))
+
+
+def rhqr_blas2_rgs_workspace(s, wt, n, m) -> int:
+    out = _sz()
+    _check("rhqr_blas2_rgs_workspace", load().rhqr_blas2_rgs_workspace(s, wt, n, m, ctypes.byref(out)))
+    return out.value
+
+
+def rhqr_blas2_rgs(s, W, wt, n, m, ldw, Q, ldq, R, T, S, ws, ws_bytes, info, stream=None) -> None:
+    _check("rhqr_blas2_rgs", load().rhqr_blas2_rgs(s, _ptr(W), wt, n, m, ldw, _ptr(Q), ldq, _ptr(R), _ptr(T), _ptr(S),
+                                                   _ptr(ws), ws_bytes, _ptr(info), _stream(stream)))
 
 
 def rhqr_sketch_apply_noalloc(s, m, X, xt, n, c, ldx, Z, ldz, stream=None) -> None:

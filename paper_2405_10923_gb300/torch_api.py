@@ -13,7 +13,7 @@ from . import (ALG_LEFT, ALG_REC, BF16, F16, F32, F64, GAUSSIAN, SRHT, colmajor,
                rhqr_batch_create, rhqr_batch_destroy, rhqr_batch_get_tuning, rhqr_batch_set_tuning, rhqr_batch_tune,
                rhqr_batch_workspace_size, rhqr_factor_batched, rhqr_arnoldi_begin, rhqr_arnoldi_create, rhqr_arnoldi_destroy, rhqr_arnoldi_export, rhqr_arnoldi_step,
                rhqr_default_opts, rhqr_factor, rhqr_pipeline_create, rhqr_pipeline_destroy, rhqr_pipeline_submit,
-               rhqr_pipeline_wait, rhqr_arnoldi_solution, rhqr_reconstruct, rhqr_sketch_apply, rhqr_sketch_apply_workspace,
+               rhqr_pipeline_wait, rhqr_arnoldi_solution, rhqr_blas2_rgs, rhqr_blas2_rgs_workspace, rhqr_reconstruct, rhqr_sketch_apply, rhqr_sketch_apply_workspace,
                rhqr_sketch_create, rhqr_sketch_destroy, rhqr_sketch_export, rhqr_sketch_shape, rhqr_workspace_size)
 
 TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}
@@ -139,6 +139,21 @@ class Pipeline:
             self.close()
         except Exception:
             pass
+
+
+def blas2_rgs(sk: Sketch, W: torch.Tensor):
+    """rhqr_blas2_rgs (Algorithm 9) on a column-major W; returns Q, R, T, S and info."""
+    n, m = W.shape
+    wt = dtype_code(W)
+    Q = colmajor(torch.zeros((n, m), dtype=W.dtype, device=W.device))
+    R = colmajor(torch.zeros((m, m), dtype=torch.float64, device=W.device))
+    T = colmajor(torch.zeros((m, m), dtype=torch.float64, device=W.device))
+    S = colmajor(torch.zeros((sk.k, m), dtype=torch.float64, device=W.device))
+    info = torch.zeros(4, dtype=torch.int32, device=W.device)
+    need = rhqr_blas2_rgs_workspace(sk.handle, wt, n, m)
+    ws = torch.empty(max(need, 1), dtype=torch.uint8, device=W.device)
+    rhqr_blas2_rgs(sk.handle, W, wt, n, m, ld_of(W), Q, ld_of(Q), R, T, S, ws, need, info)
+    return Q, R, T, S, info
 
 
 def reconstruct(sk: Sketch, S, T, R, Z, W, want_Q=True):
