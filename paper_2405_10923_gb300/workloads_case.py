@@ -12,11 +12,13 @@ warm-up, inputs resident on the device):
                 diffusion operator on a 1024 x 1024 grid (n = 2^20, Peclet 10),
                 SRHT k = 400, 100 steps, float64 and float32 basis; the operator
                 (torch, matrix-free) is timed with the step, as a user runs it
+  rgs         : BLAS2-RGS (Algorithm 9) of the srht_left matrix, float64 and
+                float32, SRHT k = 512 (Omega_full, no exact top block)
   gmres       : restarted RHQR-GMRES (Algorithm 8) on the same system, restart
                 100, float64, up to --cycles cycles towards 1e-8 (time per cycle
                 and the relative residual after each)
 
-python -m paper_2405_10923_gb300.workloads_case [--cases left_small srht_left srht_rec arnoldi gmres] [--reps 3]
+python -m paper_2405_10923_gb300.workloads_case [--cases left_small srht_left srht_rec rgs arnoldi gmres] [--reps 3]
 
 Accuracy is reported with the library's own sketch of the result in float64
 (orth = max |eig(I - (Psi Q)^t Psi Q)|) and resid = ||W - QR||_F / ||W||_F
@@ -48,7 +50,7 @@ def _time(fn, reps):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--cases", nargs="+", default=["left_small", "srht_left", "srht_rec", "arnoldi", "gmres"])
+    ap.add_argument("--cases", nargs="+", default=["left_small", "srht_left", "srht_rec", "rgs", "arnoldi", "gmres"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--cycles", type=int, default=5)
     a = ap.parse_args()
@@ -88,7 +90,7 @@ def main():
 
     n, m, k = 1 << 20, 128, 512
     W64 = None
-    if "srht_left" in a.cases or "srht_rec" in a.cases:
+    if "srht_left" in a.cases or "srht_rec" in a.cases or "rgs" in a.cases:
         W64 = ri.device_spectrum(n, m, 1e12, 1002, dtype=torch.float64)
         W32 = ri.device_spectrum(n, m, 1e12, 1002, dtype=torch.float32)
         sk = ta.Sketch(n, k, rh.SRHT, 2002)
@@ -111,6 +113,18 @@ def main():
             es = W.element_size()
             emit(case="srht_rec", path=f"recRHQR {name}, {passes} passes", n=n, m=m, k=k, sketch="srht", ms=ms,
                  gbps_w_factored=n * m * es / (ms * 1e-3) / 1e9, orth=orth, resid=resid)
+    if "rgs" in a.cases:
+        for W, name in ((W64, "f64"), (W32, "f32")):
+            ta.blas2_rgs(sk, W)
+            ms = _time(lambda: ta.blas2_rgs(sk, W), a.reps)
+            Q, R, T, S, info = ta.blas2_rgs(sk, W)
+            torch.cuda.synchronize()
+            G = (S.t() @ S).cpu().numpy()
+            emit(case="rgs", path="BLAS2-RGS " + name, n=n, m=m, k=k, sketch="srht", ms=ms,
+                 gbps_w_factored=n * m * W.element_size() / (ms * 1e-3) / 1e9, status=ta.read_info(info)["status"],
+                 sketched_orth=float(np.max(np.abs(np.linalg.eigvalsh(np.eye(m) - G)))),
+                 t_minus_identity=float((T - torch.eye(m, dtype=T.dtype, device=T.device)).abs().max()),
+                 resid=float(torch.linalg.norm(W.double() - Q.double() @ R) / torch.linalg.norm(W.double())))
     if "arnoldi" in a.cases:
         g = 1024
         n, mmax, k = g * g, 100, 400
