@@ -141,7 +141,9 @@ rhqr_status rhqr_workspace_size(rhqr_sketch s, int64_t n, int32_t m, int32_t wt,
  *   X : n x c, dtype xt (F64 or F32), leading dimension ldx >= n
  *   Z : (k+m) x c float64, leading dimension ldz >= k+m (output)
  * The top m rows are exact copies; the bottom k rows are the sketch.
- * Requires 0 <= m < n, m <= k.
+ * Requires 0 <= m < n, m <= k.  There is no device status record: if a bounded
+ * wait of the tensor-core kernel (float32 X, 16-bit Gaussian operator) runs
+ * out, the bottom k rows of Z are NaN.
  */
 rhqr_status rhqr_sketch_apply(rhqr_sketch s, int32_t m, const void *X, int32_t xt, int64_t n,
                               int32_t c, int64_t ldx, double *Z, int64_t ldz, void *ws,
@@ -303,8 +305,8 @@ rhqr_status rhqr_batch_set_tuning(rhqr_batch b, const int32_t *choice /* host, 3
  *   S : k x m float64 (ld = k) = Omega Q;  info : device rhqr_info (a zero or
  *   non-finite rho is reported with its column).
  * ws/ws_bytes : device workspace of at least rhqr_blas2_rgs_workspace bytes.
- * Requires 1 <= m <= 1024, n > m, and for the Gaussian kind n equal to the
- * sketch's n.
+ * Requires 1 <= m <= 1024, m <= k, n > m, and for the Gaussian kind n equal
+ * to the sketch's n (else RHQR_EINVAL).
  */
 rhqr_status rhqr_blas2_rgs_workspace(rhqr_sketch s, int32_t wt, int64_t n, int32_t m, size_t *bytes);
 rhqr_status rhqr_blas2_rgs(rhqr_sketch s, const void *W, int32_t wt, int64_t n, int32_t m, int64_t ldw, void *Q,
@@ -347,21 +349,23 @@ rhqr_status rhqr_pipeline_wait(rhqr_pipeline p);
 rhqr_status rhqr_pipeline_destroy(rhqr_pipeline p);
 
 /*
- * rhqr_sketch_apply_noalloc -- rhqr_sketch_apply (Algorithm 1) without a
- * caller workspace; the paper has no counterpart.  For callers that cannot
- * allocate device memory when they call: code running inside a CUDA-graph
- * capture or a framework hook where cudaMalloc is forbidden or would break
- * the capture, real-time paths that must not block on the allocator, and
- * hosts that own all device memory and cannot hand the library a workspace.
- * Arguments as for rhqr_sketch_apply (X and Z are still the caller's).
+ * rhqr_sketch_apply_noalloc -- rhqr_sketch_apply without a caller workspace;
+ * the paper has no counterpart.  For callers that cannot allocate device
+ * memory when they call: framework hooks and custom operators whose rules
+ * forbid device allocation at call time, real-time paths that must not block
+ * on cudaMalloc, and host applications that own all device memory and cannot
+ * hand the library a workspace.  Arguments as for rhqr_sketch_apply (X and Z
+ * are still the caller's).
  * Scratch: a fixed RHQR_NOALLOC_SCRATCH_BYTES device array inside the library
  * that every GPU loading the library holds until the process exits; a call
  * needing more scratch (large k * c) returns RHQR_ENOMEM and does nothing.
  * The call allocates nothing.  Its first call on a device looks up the
- * array's device address (with that device current), so make that first call
- * before any stream capture.  All calls share the array, which keeps the last
- * call's contents; calls whose work overlaps on the GPU (several streams or
- * threads) race on it and must be serialised by the caller.
+ * array's device address (with that device current) and caches it with the
+ * device's current CUDA context; a call from another context of the device
+ * (after cudaDeviceReset, for instance) looks it up again.  Make that first
+ * call before any stream capture.  All calls share the array, which keeps the
+ * last call's contents; calls whose work overlaps on the GPU (several streams
+ * or threads) race on it and must be serialised by the caller.
  */
 #define RHQR_NOALLOC_SCRATCH_BYTES (24u * 1024u * 1024u)
 rhqr_status rhqr_sketch_apply_noalloc(rhqr_sketch s, int32_t m, const void *X, int32_t xt, int64_t n, int32_t c,

@@ -33,8 +33,6 @@ namespace rhqr {
 
 const SketchView *sketch_view_of(rhqr_sketch s) { return &s->view; }
 
-static const long long kDefaultBudget = 20000000LL;
-
 static bool valid_dtype_hd(int32_t t) { return t == RHQR_F64 || t == RHQR_F32; }
 static bool valid_dtype_any(int32_t t) { return t >= RHQR_F64 && t <= RHQR_F16; }
 
@@ -268,7 +266,8 @@ rhqr_status rhqr_sketch_apply(rhqr_sketch s, int32_t m, const void *X, int32_t x
   if (ldx < n || ldz < (int64_t)s->view.k + m) return RHQR_EINVAL;
   // float32 data with a 16-bit Gaussian operator: tensor cores, exact 3-limb split
   if (xt == RHQR_F32 && sketch_tc_supported(s->view, n, m, c) && ldx % 4 == 0 && ((uintptr_t)X % 16) == 0)
-    return sketch_apply_tc(s->view, m, (const float *)X, n, c, ldx, 3, Z, ldz, ws, ws_bytes, (cudaStream_t)stream);
+    return sketch_apply_tc(s->view, m, (const float *)X, n, c, ldx, 3, Z, ldz, ws, ws_bytes, nullptr, 0,
+                           (cudaStream_t)stream);
   return sketch_apply_simt(s->view, m, X, xt, n, c, ldx, Z, ldz, ws, ws_bytes, (cudaStream_t)stream);
 }
 
@@ -283,7 +282,6 @@ struct RecBuffers {
   char *TriT, *GT;
   float *TriT64;  // padded to a multiple of the tensor-core panel width
   double *Rinv;   // R^{-1} of the pass (tensor-core product solve)
-  int *err;
   char *hqr_ws;
   size_t hqr_bytes;
   char *sk_ws;
@@ -318,7 +316,6 @@ static rhqr_status carve_rec(Carver &c, const SketchView &v, int64_t n, int32_t 
     int64_t mp64 = ceil_div(m, kSolvePanel) * kSolvePanel;
     b.TriT64 = c.take<float>((size_t)mp64 * mp64);
     b.Rinv = c.take<double>((size_t)m * m);
-    b.err = c.take<int>(4);
   }
   b.hqr_bytes = hqr_workspace_bytes(p, m);
   b.hqr_ws = c.take<char>(b.hqr_bytes);
@@ -328,10 +325,11 @@ static rhqr_status carve_rec(Carver &c, const SketchView &v, int64_t n, int32_t 
 }
 
 static rhqr_status sketch_for_pass(const SketchView &v, int32_t m, const void *X, int32_t wt, int64_t n,
-                                   int64_t ldx, double *Z, int64_t ldz, int limbs, RecBuffers &b, cudaStream_t st) {
+                                   int64_t ldx, double *Z, int64_t ldz, int limbs, RecBuffers &b, rhqr_info *info,
+                                   long long budget, cudaStream_t st) {
   if (v.kind == RHQR_SKETCH_GAUSSIAN && (v.omega_dtype == RHQR_BF16 || v.omega_dtype == RHQR_F16) &&
       wt == RHQR_F32 && sketch_tc_supported(v, n, m, m)) {
-    return sketch_apply_tc(v, m, (const float *)X, n, m, ldx, limbs, Z, ldz, b.sk_ws, b.sk_bytes, st);
+    return sketch_apply_tc(v, m, (const float *)X, n, m, ldx, limbs, Z, ldz, b.sk_ws, b.sk_bytes, info, budget, st);
   }
   return sketch_apply_simt(v, m, X, wt, n, m, ldx, Z, ldz, b.sk_ws, b.sk_bytes, st);
 }
@@ -354,7 +352,7 @@ rhqr_status solve_rows<float>(const float *X, int64_t ldx, int64_t n, int32_t m,
   if (solve_tc_supported(m)) {
     int32_t mp64 = (int32_t)(ceil_div(m, kSolvePanel) * kSolvePanel);
     RHQR_TRY(pad_transpose_to<float>(Tri, m, mp64, 1, b.TriT64, st));
-    return rows_solve_tc(X, ldx, 0, n, m, b.TriT64, mp64, Q, ldq, b.err, st);
+    return rows_solve_tc(X, ldx, 0, n, m, b.TriT64, mp64, Q, ldq, info, budget, st);
   }
   RHQR_TRY(pad_transpose<float>(Tri, m, 1, (float *)b.TriT, st));
   return rows_solve<float>(X, ldx, 0, n, m, (const float *)b.TriT, Q, ldq, st);
@@ -373,7 +371,7 @@ static rhqr_status rec_typed(const SketchView &v, const T *W, int32_t wt, int64_
                              const rhqr_opts &o, T *U, int64_t ldu, double *S, int64_t lds, double *Tm, double *R,
                              T *Q, int64_t ldq, RecBuffers &b, rhqr_info *info, cudaStream_t st) {
   const int64_t p = (int64_t)v.k + m;
-  const long long budget = o.wait_budget > 0 ? o.wait_budget : kDefaultBudget;
+  const long long budget = o.wait_budget > 0 ? o.wait_budget : kDefaultWaitBudget;
   const T *X = W;
   int64_t ldx = ldw;
   for (int pass = 0; pass < o.passes; ++pass) {
@@ -381,7 +379,7 @@ static rhqr_status rec_typed(const SketchView &v, const T *W, int32_t wt, int64_
     int limbs = pass == 0 ? o.limbs_first : o.limbs_refine;
     {
       PhaseScope ps(PH_SKETCH, st);
-      RHQR_TRY(sketch_for_pass(v, m, X, wt, n, ldx, b.Z, p, limbs, b, st));
+      RHQR_TRY(sketch_for_pass(v, m, X, wt, n, ldx, b.Z, p, limbs, b, info, budget, st));
     }
     double *Sdst = last ? S : b.Spass;
     int64_t ldsd = last ? lds : p;

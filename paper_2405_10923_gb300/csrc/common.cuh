@@ -45,6 +45,10 @@ struct PhaseScope {
   ~PhaseScope();
 };
 
+// Polls of a device-side wait before it gives up with RHQR_ETIMEOUT, unless
+// the caller sets rhqr_opts.wait_budget.
+constexpr long long kDefaultWaitBudget = 20000000LL;
+
 inline size_t dtype_size(int32_t t) {
   switch (t) {
     case RHQR_F64: return 8;

@@ -146,7 +146,8 @@ extern "C" {
 rhqr_status rhqr_blas2_rgs_workspace(rhqr_sketch s, int32_t wt, int64_t n, int32_t m, size_t *bytes) {
   if (s == nullptr || bytes == nullptr || (wt != RHQR_F64 && wt != RHQR_F32) || m < 1 || n <= m) return RHQR_EINVAL;
   const SketchView &v = *sketch_view_of(s);
-  if (m > 1024 || (v.kind == RHQR_SKETCH_GAUSSIAN && n != v.n) || (v.kind == RHQR_SKETCH_SRHT && n > v.N))
+  // Omega Q (k x m) can only have orthonormal columns when k >= m
+  if (m > 1024 || m > v.k || (v.kind == RHQR_SKETCH_GAUSSIAN && n != v.n) || (v.kind == RHQR_SKETCH_SRHT && n > v.N))
     return RHQR_EINVAL;
   *bytes = rgs_workspace(v, wt, n, m);
   return RHQR_OK;

@@ -35,6 +35,8 @@
 #include <cudaTypedefs.h>
 
 #include "sketch_tc.cuh"
+#include "tcgen05.cuh"
+#include "tma_host.cuh"
 
 namespace rhqr {
 namespace tc {
@@ -64,140 +66,6 @@ struct Params {
   int *err;
   long long budget;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait.  Returns false if the block is aborting or the budget ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long budget, int *err,
-                                          volatile int *abort_s) {
-  long long it = 0;
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort_s) return false;
-    if (++it > budget) {
-      atomicExch(err, 1);
-      *abort_s = 1;
-      return false;
-    }
-  }
-  return true;
-}
-// warp-uniform bounded wait (every lane polls, the decision is unanimous)
-__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, long long budget, int *err,
-                                          volatile int *abort_s) {
-  bool ok = mbar_wait(bar, parity, budget, err, abort_s);
-  return __all_sync(0xffffffffu, ok);
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_u32(dst)),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// contiguous bulk copy global -> shared (16-byte aligned, multiple of 16 bytes)
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (bf16 or f16 inputs, f32 accumulate)
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-#define RHQR_R32(r)                                                                                              \
-  "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),    \
-      "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),     \
-      "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),    \
-      "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-#define RHQR_W32(r)                                                                                               \
-  "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),   \
-      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), \
-      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), \
-      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
-
-// 32 consecutive columns of this warp's 32 tensor-memory lanes (one per thread)
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : RHQR_R32(r)
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-      RHQR_W32(r)
-      : "memory");
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes grouped in 8-row (1024-byte) atoms.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr, uint32_t sbo = 1024) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;            // leading byte offset (unused with this swizzle)
-  d |= (uint64_t)(sbo >> 4) << 32;   // stride byte offset: next 8-row atom
-  d |= (uint64_t)1 << 46;            // descriptor version
-  d |= (uint64_t)2 << 61;            // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor of kind::f16: f32 accumulator, K-major A and B.
-__host__ __device__ constexpr uint32_t make_idesc(int M, int N, uint32_t fmt) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
 
 template <class TL>
 struct Limb;
@@ -241,6 +109,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint64_t *fresh_full = bars + 16, *fresh_empty = bars + 17;
   uint32_t *tmem_slot = (uint32_t *)(bars + 18);
   volatile int *abort_s = (volatile int *)(bars + 19);
+  uint64_t *mma_done = bars + 20;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mt = blockIdx.x, nt = blockIdx.y, ch = blockIdx.z;
@@ -262,6 +131,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     mbar_init(fresh_full, 1);
     mbar_init(fresh_empty, NUM_DRAIN_WARPS);
+    mbar_init(mma_done, 1);
     *abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -269,23 +139,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     tmem_alloc(tmem_slot, 512);
     tmem_relinquish();
   }
-  tc_fence_before();
+  fence_before();
   __syncthreads();
-  tc_fence_after();
+  fence_after();
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
     if (lane == 0) {
       int issued = 0;
-      bool aborted = false;
       for (int i = 0; i < steps; ++i) {
         const int s = i % S;
         const uint32_t ph = (uint32_t)(i / S) & 1u;
         if (!mbar_wait(empty + s, ph ^ 1u, P.budget, P.err, abort_s) ||
-            (!INPLACE && !mbar_wait(xempty + s, ph ^ 1u, P.budget, P.err, abort_s))) {
-          aborted = true;
+            (!INPLACE && !mbar_wait(xempty + s, ph ^ 1u, P.budget, P.err, abort_s)))
           break;
-        }
         uint8_t *st = smem + s * stage_bytes;
         mbar_expect_tx(full_a + s, (uint32_t)(A_BYTES + P.xbytes));
         const int xr = (int)(x_begin + (int64_t)i * BK);
@@ -293,21 +160,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         tma_load_2d(st + A_BYTES, &tmapX, full_a + s, xr, col0);
         ++issued;
       }
-      if (aborted) {  // wait (bounded) for the copies still in flight
-        for (int i = max(0, issued - S); i < issued; ++i) {
-          long long it = 0;
-          while (!mbar_try_wait(full_a + (i % S), (uint32_t)(i / S) & 1u) && ++it < P.budget) {
-          }
-        }
-      }
+      // the last copies issued into each stage complete before the block exits
+      // (already so on the normal path; after a stop they may still be in flight)
+      for (int i = max(0, issued - S); i < issued; ++i) drain_wait(full_a + (i % S), (uint32_t)(i / S) & 1u);
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(128, BM, Limb<TL>::fmt);  // M: 128 columns of X, N: 256 rows of G
+      const uint32_t idesc = idesc_f16(128, BM, Limb<TL>::fmt);  // M: 128 columns of X, N: 256 rows of G
       int i = 0;
       for (int d = 0; d < drains && i < steps; ++d) {
         if (d > 0 && !mbar_wait(fresh_empty, (uint32_t)(d - 1) & 1u, P.budget, P.err, abort_s)) break;
-        tc_fence_after();
+        fence_after();
         bool ok = true;
         for (int j = 0; j < per_drain && i < steps; ++j, ++i) {
           const int s = i % S;
@@ -317,7 +180,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             ok = false;
             break;
           }
-          tc_fence_after();
+          fence_after();
           // descriptors advance by (byte offset >> 4): the loops unroll to constant adds
           const uint32_t st_base = smem_u32(smem + s * stage_bytes);
           const uint64_t gd0 = sw128_desc(st_base);  // G: 256 rows of 128 bytes
@@ -327,13 +190,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           for (int kk = 0; kk < BK / 16; ++kk)
 #pragma unroll
             for (int l = 0; l < L; ++l)
-              mma_f16(tmem, xd0 + (uint64_t)((l * LIMB_STRIDE + kk * 32) >> 4), gd0 + (uint64_t)((kk * 32) >> 4),
+              mma_ss(tmem, xd0 + (uint64_t)((l * LIMB_STRIDE + kk * 32) >> 4), gd0 + (uint64_t)((kk * 32) >> 4),
                       idesc, (uint32_t)(j != 0 || kk != 0 || l != 0));
           mma_commit(empty + s);
         }
         mma_commit(fresh_full);
         if (!ok) break;
       }
+      mma_quiesce(mma_done);  // no MMA in flight when tensor memory is released
     }
   } else if (warp >= CONV_WARP0 && warp < CONV_WARP0 + NUM_CONV_WARPS) {
     // converters: 128 threads, X staging (col-major 64 rows x Nt) -> limbs
@@ -439,7 +303,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         ok = false;
         break;
       }
-      tc_fence_after();
+      fence_after();
       const bool last = (d == drains - 1);
       for (int c0 = 0; c0 < 128; c0 += 32) {
         uint32_t f[32], r[32];
@@ -464,16 +328,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
       }
       tmem_wait_st();
-      tc_fence_before();
+      fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(fresh_empty);
     }
     (void)ok;
   }
-  tc_fence_before();
+  fence_before();
   __syncthreads();
   if (warp == 1) {
-    tc_fence_after();
+    fence_after();
     tmem_dealloc(tmem, 512);
   }
 }
@@ -486,15 +350,20 @@ static rhqr_status launch_sketch(dim3 grid, size_t smem, cudaStream_t st, const 
   return RHQR_OK;
 }
 
-// Z[ztop + r, col] = scale * sum_chunk part[chunk][r][col]  (float64, fixed order)
+// Z[ztop + r, col] = scale * sum_chunk part[chunk][r][col]  (float64, fixed order).
+// If a wait of the sketch kernel ran out (*err != 0) its partials are
+// incomplete: the sketch rows are set to NaN and RHQR_ETIMEOUT is recorded in
+// info (when given), so the failure cannot pass for a result.
 __global__ void reduce_part_kernel(const float *part, int32_t nch, int32_t k, int32_t c, int32_t ztop, double scale,
-                                   double *Z, int64_t ldz) {
+                                   double *Z, int64_t ldz, const int *err, rhqr_info *info) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)k * c) return;
+  const bool failed = *err != 0;
+  if (failed && idx == 0) set_status(info, RHQR_ETIMEOUT, -1);
   double acc = 0.0;
   for (int ch = 0; ch < nch; ++ch) acc += (double)part[(int64_t)ch * k * c + idx];
   int64_t r = idx / c, col = idx - r * c;
-  Z[col * ldz + ztop + r] = acc * scale;
+  Z[col * ldz + ztop + r] = failed ? __longlong_as_double(0x7ff8000000000000LL) : acc * scale;
 }
 
 __global__ void copy_top_f32_kernel(const float *X, int64_t ldx, int32_t m, int32_t c, double *Z, int64_t ldz) {
@@ -550,21 +419,6 @@ rhqr_status make_operator_tiles(const void *G, int64_t ldg, int64_t n, int32_t k
   return RHQR_OK;
 }
 
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (fn == nullptr) {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    else
-      (void)cudaGetLastError();
-  }
-  return fn;
-}
-
 // Work split: the CTAs of one launch cover (k/256) x (c/Nt) tiles times nch
 // K-chunks; nch is chosen so the grid fills the 152 SMs in whole waves.
 static int64_t tc_nchunks(const SketchView &s, int64_t n, int32_t m, int32_t c, int64_t *kchunk) {
@@ -584,7 +438,7 @@ bool sketch_tc_supported(const SketchView &s, int64_t n, int32_t m, int32_t c) {
   if (s.omega_dtype != RHQR_BF16 && s.omega_dtype != RHQR_F16) return false;
   if (c < 1 || c > tc::MAXC || m < 0 || n <= m || n > (int64_t(1) << 31) - 1) return false;
   if (s.Gt == nullptr || s.gt_nkb != operator_tiles_nkb(n)) return false;
-  return tensor_map_encoder() != nullptr;
+  return tensor_map_encode_fn() != nullptr;
 }
 
 size_t sketch_tc_workspace_bytes(const SketchView &s, int64_t n, int32_t m, int32_t c) {
@@ -593,7 +447,8 @@ size_t sketch_tc_workspace_bytes(const SketchView &s, int64_t n, int32_t m, int3
 }
 
 rhqr_status sketch_apply_tc(const SketchView &s, int32_t m, const float *X, int64_t n, int32_t c, int64_t ldx,
-                            int limbs, double *Z, int64_t ldz, void *ws, size_t ws_bytes, cudaStream_t st) {
+                            int limbs, double *Z, int64_t ldz, void *ws, size_t ws_bytes, rhqr_info *info,
+                            long long budget, cudaStream_t st) {
   if (!sketch_tc_supported(s, n, m, c)) return RHQR_ENOTSUP;
   if (limbs < 1 || limbs > 3) return RHQR_EINVAL;
   if ((ldx % 4) != 0 || ((uintptr_t)X % 16) != 0) return RHQR_ENOTSUP;
@@ -613,7 +468,7 @@ rhqr_status sketch_apply_tc(const SketchView &s, int32_t m, const float *X, int6
     cuuint64_t strides[1] = {(cuuint64_t)ldx * 4};
     cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)Nt};
     cuuint32_t estr[2] = {1, 1};
-    CUresult cr = tensor_map_encoder()(&mapX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), dims,
+    CUresult cr = tensor_map_encode_fn()(&mapX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), dims,
                                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) return RHQR_ECUDA;
@@ -635,7 +490,7 @@ rhqr_status sketch_apply_tc(const SketchView &s, int32_t m, const float *X, int6
   P.gt = (const char *)s.Gt;
   P.gt_nkb = s.gt_nkb;
   P.err = err;
-  P.budget = 4000000LL;
+  P.budget = budget > 0 ? budget : kDefaultWaitBudget;
   const size_t stage_bytes = tc::A_BYTES + tc::X_BYTES + (limbs <= 2 ? 0 : (size_t)limbs * tc::B_BYTES);
   size_t smem = 1024 + (size_t)P.stages * stage_bytes + 256;
   dim3 grid((unsigned)ceil_div(s.k, tc::BM), (unsigned)ceil_div(Np, Nt), (unsigned)nch);
@@ -658,7 +513,7 @@ rhqr_status sketch_apply_tc(const SketchView &s, int32_t m, const float *X, int6
   }
   int64_t tot = (int64_t)s.k * c;
   tc::reduce_part_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(part, (int32_t)nch, s.k, c, m,
-                                                                       1.0 / sqrt((double)s.k), Z, ldz);
+                                                                       1.0 / sqrt((double)s.k), Z, ldz, err, info);
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }

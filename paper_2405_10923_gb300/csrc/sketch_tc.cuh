@@ -20,8 +20,11 @@ int64_t operator_tiles_nkb(int64_t n);
 rhqr_status make_operator_tiles(const void *G, int64_t ldg, int64_t n, int32_t k, void *Gt, cudaStream_t st);
 
 // Z = Psi_m X for float32 X (n x c, ldx) with the bf16/f16 Gaussian operator;
-// X is split into `limbs` 16-bit terms (1..3).
+// X is split into `limbs` 16-bit terms (1..3).  Every wait of the kernel gives
+// up after `budget` polls (<= 0: kDefaultWaitBudget); a wait that ran out
+// leaves NaN in the sketch rows of Z and RHQR_ETIMEOUT in info (may be NULL).
 rhqr_status sketch_apply_tc(const SketchView &s, int32_t m, const float *X, int64_t n, int32_t c, int64_t ldx,
-                            int limbs, double *Z, int64_t ldz, void *ws, size_t ws_bytes, cudaStream_t st);
+                            int limbs, double *Z, int64_t ldz, void *ws, size_t ws_bytes, rhqr_info *info,
+                            long long budget, cudaStream_t st);
 
 }  // namespace rhqr

@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   int *err_s = reinterpret_cast<int *>(tmem_slot + 2);
   unsigned int *fmax_s = tmem_slot + 3;  // max |F| of this CTA's blocks (float bits, >= 0)
   uint32_t *peer_cnt = tmem_slot + 4;    // [2]: rows read by the peer's loader groups
+  uint64_t *mma_done = bars + 16;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = P.split ? tc::cluster_ctarank() : 0u;
@@ -195,6 +196,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       tc::mbar_init(x_full + s, 1);
       tc::mbar_init(x_empty + s, 4);
     }
+    tc::mbar_init(mma_done, 1);
     *abort_s = 0;
     *err_s = 0;
     *fmax_s = 0u;
@@ -310,6 +312,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (!ok) break;
         tc::mma_commit(acc_full + b);
       }
+      tc::mma_quiesce(mma_done);  // no MMA in flight when tensor memory is released
     }
     __syncwarp();
   } else if (warp == 2) {
@@ -332,13 +335,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           // same chunk of this CTA's next tile is brought into L2 a tile ahead
           if (t + tstep < ntiles) tc::tma_prefetch_2d(&tmapX, (int)((t + tstep) * TILE), kc * 64);
         }
-      if (!ok) {  // wait (bounded) for the copies still in flight before the CTA exits
-        for (int s = 0; s < 2; ++s) {
-          long long it = 0;
-          while (last_u[s] >= 0 && !tc::mbar_try_wait(x_full + s, (uint32_t)last_u[s] & 1u) && ++it < P.budget) {
-          }
-        }
-      }
+      // the last copy into each stage completes before the CTA exits (already so
+      // on the normal path; after a stop it may still be in flight)
+      for (int s = 0; s < 2; ++s)
+        if (last_u[s] >= 0) tc::drain_wait(x_full + s, (uint32_t)last_u[s] & 1u);
     }
     __syncwarp();
   } else if (warp >= LOAD_WARP0 && warp < EPI_WARP0) {
@@ -547,7 +547,7 @@ static bool make_plan(const int *own, int nown, int mp, CtaPlan &C) {
 }
 
 static size_t smem_bytes(int bregion) {
-  return 1024 + (size_t)bregion + 2 * XST_BYTES + 2 * YST_BYTES + MAXM * 4 + 12 * 8 + 64;
+  return 1024 + (size_t)bregion + 2 * XST_BYTES + 2 * YST_BYTES + MAXM * 4 + 17 * 8 + 64;
 }
 
 // Column chunks of the one or two CTAs per tile and the shared-memory size.

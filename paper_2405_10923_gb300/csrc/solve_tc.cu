@@ -23,9 +23,11 @@
 // thread per tile row) load X, finish each panel, store Q and write the Y
 // limbs.  All mbarrier waits are bounded.
 #include "solve_tc.cuh"
+#include "tcgen05.cuh"
 
 namespace rhqr {
 namespace stc {
+using namespace tc;
 
 constexpr int TILE = 128;
 constexpr int PW = 64;    // panel width
@@ -48,122 +50,9 @@ struct Params {
   int32_t m, P;        // columns, panels (P = ceil(m / 64))
   const float *TriT;   // mp x mp row-major: TriT[l * mp + j] = Tri[l, j], identity-padded
   int32_t mp;
-  int *err;
+  rhqr_info *info;
   long long budget;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long budget, int *err,
-                                          volatile int *abort_s) {
-  long long it = 0;
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort_s) return false;
-    if (++it > budget) {
-      atomicExch(err, 1);
-      *abort_s = 1;
-      return false;
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, long long budget, int *err,
-                                          volatile int *abort_s) {
-  bool ok = mbar_wait(bar, parity, budget, err, abort_s);
-  return __all_sync(0xffffffffu, ok);
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-// D[tmem] (+)= A[tmem] * B[smem]^T, kind::f16, bf16 inputs, f32 accumulate
-__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
-                                       uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-#define STC_R32(r)                                                                                               \
-  "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),    \
-      "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),     \
-      "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),    \
-      "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-#define STC_W32(r)                                                                                                \
-  "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),   \
-      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), \
-      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), \
-      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : STC_R32(r)
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-      STC_W32(r)
-      : "memory");
-}
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16};" ::"r"(taddr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
-      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
-      : "memory");
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
 
 // index of the off-diagonal block (I, J), I < J < 4, in 0..5
 __host__ __device__ constexpr int blk_index(int I, int J) { return J * (J - 1) / 2 + I; }
@@ -186,6 +75,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_tc_kernel(Params P) {
   uint64_t *y_ready = bars, *d_ready = bars + 1, *d_free = bars + 2;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3);
   volatile int *abort_s = reinterpret_cast<volatile int *>(bars + 4);
+  int *err_s = reinterpret_cast<int *>(bars + 5);
+  uint64_t *mma_done = bars + 6;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int NP = P.P, mp = P.mp;
@@ -229,16 +120,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_tc_kernel(Params P) {
     mbar_init(y_ready, 4);
     mbar_init(d_ready, 1);
     mbar_init(d_free, 4);
+    mbar_init(mma_done, 1);
     *abort_s = 0;
+    *err_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     tmem_alloc(tmem_slot, 512);
     tmem_relinquish();
   }
-  tc_fence_before();
+  fence_before();
   __syncthreads();
-  tc_fence_after();
+  fence_after();
   const uint32_t tmem = *tmem_slot;
 
   const int64_t ntiles = (P.nrows + TILE - 1) / TILE;
@@ -252,10 +145,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_tc_kernel(Params P) {
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         for (int J = 1; J < NP; ++J) {
-          if (!mbar_wait(y_ready, ny & 1u, P.budget, P.err, abort_s)) { ok = false; break; }
+          if (!mbar_wait(y_ready, ny & 1u, P.budget, err_s, abort_s)) { ok = false; break; }
           ++ny;
-          if (!mbar_wait(d_free, (nd & 1u) ^ 1u, P.budget, P.err, abort_s)) { ok = false; break; }
-          tc_fence_after();
+          if (!mbar_wait(d_free, (nd & 1u) ^ 1u, P.budget, err_s, abort_s)) { ok = false; break; }
+          fence_after();
           int first = 1;
           for (int pr = 0; pr < 6; ++pr)
             for (int I = 0; I < J; ++I)
@@ -270,6 +163,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_tc_kernel(Params P) {
           ++nd;
         }
       }
+      mma_quiesce(mma_done);  // no MMA in flight when tensor memory is released
     }
   } else if (warp >= SOLVE_WARP0) {
     const int qd = warp & 3;
@@ -288,8 +182,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_tc_kernel(Params P) {
           v[c] = (live && col < P.m) ? __ldg(P.X + (int64_t)col * P.ldx + row) : 0.f;
         }
         if (J > 0) {
-          if (!warp_wait(d_ready, nd & 1u, P.budget, P.err, abort_s)) { ok = false; break; }
-          tc_fence_after();
+          if (!warp_wait(d_ready, nd & 1u, P.budget, err_s, abort_s)) { ok = false; break; }
+          fence_after();
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             uint32_t d[32];
@@ -298,7 +192,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_tc_kernel(Params P) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[h * 32 + j] -= __uint_as_float(d[j]);
           }
-          tc_fence_before();
+          fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(d_free);
           ++nd;
@@ -345,7 +239,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_tc_kernel(Params P) {
             tmem_st16(col + (uint32_t)(2 * MAXP * 32), w2);
           }
           tmem_wait_st();
-          tc_fence_before();
+          fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(y_ready);
           ++ny;
@@ -354,12 +248,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_tc_kernel(Params P) {
     }
     (void)ny;
   }
-  tc_fence_before();
+  fence_before();
   __syncthreads();
   if (warp == 1) {
-    tc_fence_after();
+    fence_after();
     tmem_dealloc(tmem, 512);
   }
+  if (threadIdx.x == 0 && *err_s) set_status(P.info, RHQR_ETIMEOUT, -1);
 }
 
 }  // namespace stc
@@ -367,7 +262,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) solve_tc_kernel(Params P) {
 bool solve_tc_supported(int32_t m) { return m >= 1 && m <= stc::MAXP * stc::PW; }
 
 rhqr_status rows_solve_tc(const float *X, int64_t ldx, int64_t row_begin, int64_t nrows, int32_t m,
-                          const float *TriT, int32_t mp_tri, float *Y, int64_t ldy, int *err, cudaStream_t st) {
+                          const float *TriT, int32_t mp_tri, float *Y, int64_t ldy, rhqr_info *info, long long budget,
+                          cudaStream_t st) {
   if (nrows <= 0) return RHQR_OK;
   if (!solve_tc_supported(m)) return RHQR_ENOTSUP;
   stc::Params P;
@@ -381,8 +277,8 @@ rhqr_status rows_solve_tc(const float *X, int64_t ldx, int64_t row_begin, int64_
   P.P = (int32_t)ceil_div(m, stc::PW);
   P.TriT = TriT;
   P.mp = mp_tri;
-  P.err = err;
-  P.budget = 4000000LL;
+  P.info = info;
+  P.budget = budget > 0 ? budget : kDefaultWaitBudget;
   if (P.mp < P.P * stc::PW) return RHQR_EINVAL;
   static int sms = 0;
   if (sms == 0) {
@@ -393,9 +289,8 @@ rhqr_status rows_solve_tc(const float *X, int64_t ldx, int64_t row_begin, int64_
   }
   const int64_t ntiles = ceil_div(nrows, stc::TILE);
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, sms);
-  const size_t smem = 1024 + stc::OFFDIAG_BYTES + stc::DIAG_BYTES + stc::RDIAG_BYTES + 128;
+  const size_t smem = 1024 + stc::OFFDIAG_BYTES + stc::DIAG_BYTES + stc::RDIAG_BYTES + 256;
   RHQR_CUDA_TRY(cudaFuncSetAttribute(stc::solve_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  RHQR_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
   stc::solve_tc_kernel<<<grid, stc::NUM_THREADS, smem, st>>>(P);
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;

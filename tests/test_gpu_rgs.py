@@ -50,3 +50,17 @@ def test_blas2_rgs_float32(gpu_lib):
     assert np.max(np.abs(R.cpu().numpy() - Ro)) <= 1e-5 * np.abs(Ro).max()
     assert np.max(np.abs(Q.double().cpu().numpy() - Qo)) <= 1e-5 * np.abs(Qo).max()
     sk.close()
+
+
+def test_blas2_rgs_rejects_more_columns_than_sketch_rows(gpu_lib):
+    """Omega Q (k x m) cannot have orthonormal columns when m > k: the call is
+    an argument error, reported before any device work."""
+    from paper_2405_10923_gb300 import torch_api as ta
+
+    n, k = 1000, 8
+    sk = ta.Sketch(n, k, gpu_lib.SRHT, 63)
+    assert gpu_lib.rhqr_blas2_rgs_workspace(sk.handle, gpu_lib.F64, n, k) > 0
+    with pytest.raises(gpu_lib.RHQRError) as e:
+        gpu_lib.rhqr_blas2_rgs_workspace(sk.handle, gpu_lib.F64, n, k + 1)
+    assert e.value.code == 1  # RHQR_EINVAL
+    sk.close()
