@@ -10,8 +10,10 @@ D0.  For both solves, one pass and three passes, the factorisation error
 ||W - QR||_F / ||W||_F must stay at the float32 tolerance (1e-5), and after
 three passes the sketch orthogonality ||I - (Psi Q)^t Psi Q||_2 as well, both
 measured with the oracle's FP64 sketch.  The one-pass R is also compared with
-the oracle's recRHQR R: the two Householder factorisations of the same Psi W
-agree to the sketch's rounding (float64 sketches of float32 data).
+the oracle's recRHQR R: the GPU sketches float32 data with the SRHT in float32
+arithmetic, whose error is at most gamma_{log2 N + 5} of float32 relative to
+each column (the SRHT error lemma of Section 4), about 1.2e-6 for N = 2^15;
+the Householder QR of the sketch passes that on to R column by column.
 """
 
 import numpy as np
@@ -62,5 +64,7 @@ def test_graded_inputs(gpu_lib, kind, passes, solve):
         assert metrics.sketch_orthogonality(Q, osk) <= 1e-5
     else:
         _U, _S, _T, Ro, _M = rhqr.rec_rhqr(W, osk)
-        assert metrics.r_relative_difference(R, Ro) <= 1e-10
+        u32 = 2.0**-24
+        gamma = (15 + 5) * u32 / (1 - (15 + 5) * u32)
+        assert metrics.r_relative_difference(R, Ro) <= gamma
     sk.close()
