@@ -46,7 +46,7 @@ typedef enum {
 
 typedef enum { RHQR_SKETCH_GAUSSIAN = 0, RHQR_SKETCH_SRHT = 1 } rhqr_sketch_kind;
 typedef enum { RHQR_F64 = 0, RHQR_F32 = 1, RHQR_BF16 = 2, RHQR_F16 = 3 } rhqr_dtype;
-typedef enum { RHQR_ALG_LEFT = 0, RHQR_ALG_REC = 1 } rhqr_alg;
+typedef enum { RHQR_ALG_LEFT = 0, RHQR_ALG_REC = 1, RHQR_ALG_BLOCK = 2 } rhqr_alg;
 
 /* Opaque, library-owned sketch operator (device arrays inside). */
 typedef struct rhqr_sketch_s *rhqr_sketch;
@@ -76,6 +76,10 @@ typedef struct {
                            + X E (default), 1 = tensor-core row-wise substitution  */
   int64_t wait_budget;  /* spin iterations of a device-side wait before it gives up
                            with RHQR_ETIMEOUT (0 = library default)                */
+  int32_t block_size;   /* columns per block of RHQR_ALG_BLOCK (1..64, default 32) */
+  int32_t column_scaling; /* recRHQR: 1 = equilibrate the columns of each pass's
+                           sketch Z to unit norm before its Householder QR and
+                           undo the scaling in R (default 0)                     */
 } rhqr_opts;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -154,6 +158,13 @@ rhqr_status rhqr_sketch_apply(rhqr_sketch s, int32_t m, const void *X, int32_t x
  *  alg = RHQR_ALG_LEFT: Algorithm 4 (left-looking RHQR): column j is refreshed
  *        with the previous reflectors, w_j <- w_j - U T^t S^t Psi w_j, sketched,
  *        and its randomized Householder vector taken (Algorithm 2).
+ *  alg = RHQR_ALG_BLOCK: Algorithm 5 (blockRHQR): the columns in blocks of
+ *        opts->block_size; each block is first refreshed with every earlier
+ *        block in turn (Y = Psi W_blk, W_blk <- W_blk - U_k T_k^t S_k^t Y, the
+ *        block re-sketched each time), then factored by Algorithm 4 with its
+ *        own reflectors.  T is returned as the compact-form T of all m
+ *        reflectors (T^{-1} = sut(S^t S) + diag(1/beta), eq. generalwoodburry);
+ *        its diagonal blocks are the blocks' T^(j) of Algorithm 5.
  *  alg = RHQR_ALG_REC : Algorithm 6 (recRHQR): Z = Psi W, Householder QR of Z
  *        gives S, T, R, and Q = W R^{-1} (equal to [I;0] - U T U_1^t, Section 3.3)
  *        is formed by a backward-stable row-wise triangular solve; with
@@ -161,7 +172,7 @@ rhqr_status rhqr_sketch_apply(rhqr_sketch s, int32_t m, const void *X, int32_t x
  *        R = R_p ... R_1.  U (if wanted) solves W_2 = U_2 ut(T^t S^t Z) of the
  *        last pass (Algorithm 6, "backward solve").
  * Outputs (device):
- *   U  : n x m, dtype wt, ldu >= n   (required for LEFT, optional for REC)
+ *   U  : n x m, dtype wt, ldu >= n   (required for LEFT and BLOCK, optional for REC)
  *   S  : (k+m) x m float64, lds >= k+m   (= Psi U of the representation)
  *   T  : m x m float64 (upper triangular, ld = m)
  *   R  : m x m float64 (upper triangular, ld = m)

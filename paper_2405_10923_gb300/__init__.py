@@ -20,7 +20,7 @@ from . import build as _build
 
 F64, F32, BF16, F16 = 0, 1, 2, 3
 GAUSSIAN, SRHT = 0, 1
-ALG_LEFT, ALG_REC = 0, 1
+ALG_LEFT, ALG_REC, ALG_BLOCK = 0, 1, 2
 
 STATUS = {
     0: "RHQR_OK",
@@ -53,6 +53,8 @@ class rhqr_opts(ctypes.Structure):
         ("scaling", ctypes.c_int32),
         ("solve", ctypes.c_int32),
         ("wait_budget", ctypes.c_int64),
+        ("block_size", ctypes.c_int32),
+        ("column_scaling", ctypes.c_int32),
     ]
 
 

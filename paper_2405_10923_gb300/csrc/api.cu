@@ -74,6 +74,8 @@ void rhqr_default_opts(rhqr_opts *o) {
   o->want_Q = 1;
   o->scaling = 0;
   o->wait_budget = 0;
+  o->block_size = 32;
+  o->column_scaling = 0;
 }
 
 rhqr_status rhqr_sketch_create(int64_t n, int32_t k, int32_t kind, uint64_t seed, int32_t omega_dtype,
@@ -282,6 +284,7 @@ struct RecBuffers {
   char *TriT, *GT;
   float *TriT64;  // padded to a multiple of the tensor-core panel width
   double *Rinv;   // R^{-1} of the pass (tensor-core product solve)
+  double *colnorm;  // column norms of the pass's sketch (column_scaling)
   char *hqr_ws;
   size_t hqr_bytes;
   char *sk_ws;
@@ -316,6 +319,7 @@ static rhqr_status carve_rec(Carver &c, const SketchView &v, int64_t n, int32_t 
     int64_t mp64 = ceil_div(m, kSolvePanel) * kSolvePanel;
     b.TriT64 = c.take<float>((size_t)mp64 * mp64);
     b.Rinv = c.take<double>((size_t)m * m);
+    b.colnorm = c.take<double>(m);
   }
   b.hqr_bytes = hqr_workspace_bytes(p, m);
   b.hqr_ws = c.take<char>(b.hqr_bytes);
@@ -385,8 +389,15 @@ static rhqr_status rec_typed(const SketchView &v, const T *W, int32_t wt, int64_
     int64_t ldsd = last ? lds : p;
     {
       PhaseScope ps(PH_HQR, st);
+      // column equilibration: Householder QR of Z D^{-1} has the same reflectors
+      // and R D^{-1}, so R = R~ D
+      if (o.column_scaling) RHQR_TRY(equilibrate_columns(b.Z, p, p, m, b.colnorm, st));
       RHQR_TRY(householder_qr_small(b.Z, p, p, m, Sdst, ldsd, b.Rpass, b.beta, o.scaling, b.hqr_ws, b.hqr_bytes,
                                     info, budget, st));
+      if (o.column_scaling) {
+        RHQR_TRY(scale_columns(b.Rpass, m, m, m, b.colnorm, st));
+        RHQR_TRY(scale_columns(b.Z, p, p, m, b.colnorm, st));  // Z again for M = ut(T^t S^t Z)
+      }
     }
     if (pass == 0) {
       RHQR_TRY(copy_f64(b.Rpass, (int64_t)m * m, b.Racc, st));
@@ -438,6 +449,10 @@ rhqr_status rhqr_workspace_size(rhqr_sketch s, int64_t n, int32_t m, int32_t wt,
     *bytes = left_workspace_bytes(s->view, n, m, wt);
     return RHQR_OK;
   }
+  if (o.alg == RHQR_ALG_BLOCK) {
+    *bytes = block_workspace_bytes(s->view, n, m, o.block_size, wt);
+    return RHQR_OK;
+  }
   Carver c(nullptr, 0);
   RecBuffers b;
   carve_rec(c, s->view, n, m, wt, o, b);
@@ -458,9 +473,11 @@ rhqr_status rhqr_factor(rhqr_sketch s, const void *W, int32_t wt, int64_t n, int
   const int64_t p = (int64_t)s->view.k + m;
   if (ldw < n || lds < p) return RHQR_EINVAL;
   if ((o.scaling != 0 && o.scaling != 1) || (o.solve != 0 && o.solve != 1)) return RHQR_EINVAL;
-  if (o.alg != RHQR_ALG_LEFT && o.alg != RHQR_ALG_REC) return RHQR_EINVAL;
+  if (o.alg != RHQR_ALG_LEFT && o.alg != RHQR_ALG_REC && o.alg != RHQR_ALG_BLOCK) return RHQR_EINVAL;
+  if (o.alg == RHQR_ALG_BLOCK && (o.block_size < 1 || o.block_size > 64)) return RHQR_EINVAL;
+  if (o.column_scaling != 0 && o.column_scaling != 1) return RHQR_EINVAL;
   if (o.want_Q && (Q == nullptr || ldq < n)) return RHQR_EINVAL;
-  if ((o.want_U || o.alg == RHQR_ALG_LEFT) && (U == nullptr || ldu < n)) return RHQR_EINVAL;
+  if ((o.want_U || o.alg != RHQR_ALG_REC) && (U == nullptr || ldu < n)) return RHQR_EINVAL;
   if (o.alg == RHQR_ALG_REC && (o.passes < 1 || o.passes > 16)) return RHQR_EINVAL;
   if (o.alg == RHQR_ALG_REC && o.passes > 1 && !o.want_Q) return RHQR_EINVAL;  // Q holds the passes' iterates
   if (o.limbs_first < 1 || o.limbs_first > 3 || o.limbs_refine < 1 || o.limbs_refine > 3) return RHQR_EINVAL;
@@ -473,6 +490,10 @@ rhqr_status rhqr_factor(rhqr_sketch s, const void *W, int32_t wt, int64_t n, int
   if (o.alg == RHQR_ALG_LEFT) {
     return left_factor(s->view, W, wt, n, m, ldw, o.scaling, U, ldu, S, lds, T, R, o.want_Q ? Q : nullptr, ldq, ws,
                        ws_bytes, info, st);
+  }
+  if (o.alg == RHQR_ALG_BLOCK) {
+    return block_factor(s->view, W, wt, n, m, ldw, o.block_size, o.scaling, U, ldu, S, lds, T, R,
+                        o.want_Q ? Q : nullptr, ldq, ws, ws_bytes, info, st);
   }
   Carver c(ws, ws_bytes);
   RecBuffers b;

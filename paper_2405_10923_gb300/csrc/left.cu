@@ -21,14 +21,16 @@ namespace rhqr {
 
 // ---------------------------------------------------------------------------
 // step 1 / 5 helpers
-// dots: for l < nd: d[l] = S[:, l] . s_j  (if dst_d), v[l] = S[:, l] . z  (l < nv)
+// dots over the columns l = lo + t of the current block (lo = 0: all previous
+// columns): d[t] = S[:, l] . s_j (t < nd), v[t] = S[:, l] . z (t < nv)
 // ---------------------------------------------------------------------------
 __global__ void left_dots_kernel(const double *S, int64_t lds, int64_t p, int32_t j, int32_t nd, const double *z,
-                                 int32_t nv, double *d, double *v) {
+                                 int32_t nv, double *d, double *v, int32_t lo) {
   __shared__ double red[32];
-  int l = blockIdx.x;
+  const int t = blockIdx.x;  // d[t], v[t] belong to column l = lo + t
+  const int l = lo + t;
   int which = blockIdx.y;  // 0: d (against s_j), 1: v (against z)
-  if ((which == 0 && l >= nd) || (which == 1 && l >= nv)) return;
+  if ((which == 0 && t >= nd) || (which == 1 && t >= nv)) return;
   const double *a = S + (int64_t)l * lds;
   const double *b = (which == 0) ? S + (int64_t)j * lds : z;
   int64_t start = (which == 0) ? j : l;  // s_j vanishes above j, s_l above l
@@ -36,20 +38,23 @@ __global__ void left_dots_kernel(const double *S, int64_t lds, int64_t p, int32_
   for (int64_t r = start + threadIdx.x; r < p; r += blockDim.x) acc += a[r] * b[r];
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) {
-    if (which == 0) d[l] = acc;
-    else v[l] = acc;
+    if (which == 0) d[t] = acc;
+    else v[t] = acc;
   }
 }
 
-// T[:, j] from d (if j >= 0 and finishing column j), then c = T_{nc}^t v (nc values)
+// Within the block of columns lo, lo + 1, ... (lo = 0: one block of all
+// columns): T[:, j] from d (if j >= 0, finishing column j; rows above lo are
+// zero, the block's T is a diagonal block), then c = T_blk^t v for the nc
+// block columns lo .. lo + nc - 1.
 __global__ void left_tcol_coef_kernel(double *T, int32_t m, int32_t j, const double *beta, const double *d,
-                                      const double *v, int32_t nc, double *c) {
+                                      const double *v, int32_t nc, double *c, int32_t lo) {
   if (j >= 0) {
     double bj = beta[j];
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       double val = 0.0;
-      if (i < j) {
-        for (int l = i; l < j; ++l) val += T[(int64_t)l * m + i] * d[l];
+      if (i >= lo && i < j) {
+        for (int l = i; l < j; ++l) val += T[(int64_t)l * m + i] * d[l - lo];
         val = -bj * val;
       } else if (i == j) {
         val = bj;
@@ -58,10 +63,11 @@ __global__ void left_tcol_coef_kernel(double *T, int32_t m, int32_t j, const dou
     }
     __syncthreads();
   }
-  for (int l = threadIdx.x; l < nc; l += blockDim.x) {
+  for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+    const int l = lo + t;
     double acc = 0.0;
-    for (int i = 0; i <= l; ++i) acc += T[(int64_t)l * m + i] * v[i];
-    c[l] = acc;
+    for (int i = lo; i <= l; ++i) acc += T[(int64_t)l * m + i] * v[i - lo];
+    c[t] = acc;
   }
 }
 
@@ -79,6 +85,7 @@ struct ColArgs {
   const double *gamma;  // gamma[j-1] scales column j-1
   double *y;            // (k+m) sketch, rows < m written here
   int32_t unit;         // unit-diagonal scaling: u_jj = 1 exactly
+  int32_t lo;           // first column of the block whose reflectors refresh column j (0: all)
 };
 
 template <class T>
@@ -86,14 +93,14 @@ __device__ __forceinline__ T refresh_row(const ColArgs &a, int64_t i, const doub
   const T *W = (const T *)a.W;
   T *U = (T *)a.U;
   T w = W[(int64_t)a.j * a.ldw + i];
-  const int j = a.j;
-  // previous columns, the last one still unscaled
-  for (int l = 0; l + 1 < j; ++l) w -= U[(int64_t)l * a.ldu + i] * (T)c_s[l];
-  if (j >= 1) {
+  const int j = a.j, lo = a.lo;
+  // previous columns of the block, the last one still unscaled
+  for (int l = lo; l + 1 < j; ++l) w -= U[(int64_t)l * a.ldu + i] * (T)c_s[l - lo];
+  if (j - 1 >= lo) {
     T *up = U + (int64_t)(j - 1) * a.ldu + i;
     T u = (i < j - 1) ? T(0) : ((i == j - 1 && a.unit) ? T(1) : *up * inv_g);
     *up = u;
-    w -= u * (T)c_s[j - 1];
+    w -= u * (T)c_s[j - 1 - lo];
   }
   U[(int64_t)j * a.ldu + i] = w;
   return w;
@@ -106,28 +113,28 @@ __device__ __forceinline__ T refresh_row(const ColArgs &a, int64_t i, const doub
 template <class T>
 __global__ void __launch_bounds__(256) left_refresh_kernel(ColArgs a) {
   __shared__ double c_s[1024];
-  for (int l = threadIdx.x; l < a.j; l += blockDim.x) c_s[l] = a.c[l];
-  const T inv_g = (a.j >= 1) ? (T)(1.0 / a.gamma[a.j - 1]) : T(1);
+  const int j = a.j, lo = a.lo;
+  for (int l = threadIdx.x; l < j - lo; l += blockDim.x) c_s[l] = a.c[l];
+  const T inv_g = (j - 1 >= lo) ? (T)(1.0 / a.gamma[j - 1]) : T(1);
   __syncthreads();
   const T *W = (const T *)a.W;
   T *U = (T *)a.U;
-  const int j = a.j;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
     T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
-    int l = 0;
+    int l = lo;
     for (; l + 4 < j; l += 4) {
-      p0 += U[(int64_t)l * a.ldu + i] * (T)c_s[l];
-      p1 += U[(int64_t)(l + 1) * a.ldu + i] * (T)c_s[l + 1];
-      p2 += U[(int64_t)(l + 2) * a.ldu + i] * (T)c_s[l + 2];
-      p3 += U[(int64_t)(l + 3) * a.ldu + i] * (T)c_s[l + 3];
+      p0 += U[(int64_t)l * a.ldu + i] * (T)c_s[l - lo];
+      p1 += U[(int64_t)(l + 1) * a.ldu + i] * (T)c_s[l + 1 - lo];
+      p2 += U[(int64_t)(l + 2) * a.ldu + i] * (T)c_s[l + 2 - lo];
+      p3 += U[(int64_t)(l + 3) * a.ldu + i] * (T)c_s[l + 3 - lo];
     }
-    for (; l + 1 < j; ++l) p0 += U[(int64_t)l * a.ldu + i] * (T)c_s[l];
+    for (; l + 1 < j; ++l) p0 += U[(int64_t)l * a.ldu + i] * (T)c_s[l - lo];
     T w = W[(int64_t)j * a.ldw + i] - ((p0 + p1) + (p2 + p3));
-    if (j >= 1) {
+    if (j - 1 >= lo) {
       T *up = U + (int64_t)(j - 1) * a.ldu + i;
       const T u = (i < j - 1) ? T(0) : ((i == j - 1 && a.unit) ? T(1) : *up * inv_g);
       *up = u;
-      w -= u * (T)c_s[j - 1];
+      w -= u * (T)c_s[j - 1 - lo];
     }
     U[(int64_t)j * a.ldu + i] = w;
     if (i < a.m) a.y[i] = (double)w;
@@ -142,8 +149,8 @@ __global__ void left_column_srht_kernel(ColArgs a, const uint32_t *sign_bits, in
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *v = reinterpret_cast<T *>(smem_raw);
   __shared__ double c_s[1024];
-  for (int l = threadIdx.x; l < a.j; l += blockDim.x) c_s[l] = a.c[l];
-  const T inv_g = (a.j >= 1) ? (T)(1.0 / a.gamma[a.j - 1]) : T(1);
+  for (int l = threadIdx.x; l < a.j - a.lo; l += blockDim.x) c_s[l] = a.c[l];
+  const T inv_g = (a.j - 1 >= a.lo) ? (T)(1.0 / a.gamma[a.j - 1]) : T(1);
   __syncthreads();
   const int64_t row0 = (int64_t)blockIdx.x * N2;
   for (int t = threadIdx.x; t < N2; t += blockDim.x) {
@@ -201,8 +208,8 @@ __global__ void __launch_bounds__(LG_RB) left_column_gauss_kernel(ColArgs a, con
                                                                   double *part) {
   __shared__ double w_s[LG_RB];
   __shared__ double c_s[1024];
-  for (int l = threadIdx.x; l < a.j; l += blockDim.x) c_s[l] = a.c[l];
-  const T inv_g = (a.j >= 1) ? (T)(1.0 / a.gamma[a.j - 1]) : T(1);
+  for (int l = threadIdx.x; l < a.j - a.lo; l += blockDim.x) c_s[l] = a.c[l];
+  const T inv_g = (a.j - 1 >= a.lo) ? (T)(1.0 / a.gamma[a.j - 1]) : T(1);
   __syncthreads();
   const int64_t row0 = (int64_t)blockIdx.x * LG_RB;
   int64_t i = row0 + threadIdx.x;
@@ -338,15 +345,15 @@ static rhqr_status left_typed(const SketchView &s, const T *W, int64_t n, int32_
   // raw sketches of all columns (Algorithm 4 sketches w_j before refreshing it)
   RHQR_TRY(sketch_apply_simt(s, m, W, sizeof(T) == 8 ? RHQR_F64 : RHQR_F32, n, m, ldw, Zraw, p, aws, apply_ws, st));
 
-  ColArgs ca{W, ldw, U, ldu, n, m, 0, cbuf, gam, y, scaling == 0 ? 1 : 0};
+  ColArgs ca{W, ldw, U, ldu, n, m, 0, cbuf, gam, y, scaling == 0 ? 1 : 0, 0};
   const double scale = 1.0 / sqrt((double)s.k);
   for (int j = 0; j < m; ++j) {
     if (j >= 1) {
       // d_l = s_l . s_{j-1} (l < j-1) finishes column j-1 of T; v_l = s_l . z_j (l < j)
       dim3 g((unsigned)j, 2);
-      left_dots_kernel<<<g, 256, 0, st>>>(S, lds, p, j - 1, j - 1, Zraw + (int64_t)j * p, j, dbuf, vbuf);
+      left_dots_kernel<<<g, 256, 0, st>>>(S, lds, p, j - 1, j - 1, Zraw + (int64_t)j * p, j, dbuf, vbuf, 0);
       RHQR_LAUNCH_CHECK();
-      left_tcol_coef_kernel<<<1, 256, 0, st>>>(Tm, m, j - 1, beta, dbuf, vbuf, j, cbuf);
+      left_tcol_coef_kernel<<<1, 256, 0, st>>>(Tm, m, j - 1, beta, dbuf, vbuf, j, cbuf, 0);
       RHQR_LAUNCH_CHECK();
     }
     ca.j = j;
@@ -396,9 +403,9 @@ static rhqr_status left_typed(const SketchView &s, const T *W, int64_t n, int32_
   // finish T's last column and the last column's scale
   {
     dim3 g((unsigned)std::max(1, m - 1), 2);
-    left_dots_kernel<<<g, 256, 0, st>>>(S, lds, p, m - 1, m - 1, Zraw, 0, dbuf, vbuf);
+    left_dots_kernel<<<g, 256, 0, st>>>(S, lds, p, m - 1, m - 1, Zraw, 0, dbuf, vbuf, 0);
     RHQR_LAUNCH_CHECK();
-    left_tcol_coef_kernel<<<1, 256, 0, st>>>(Tm, m, m - 1, beta, dbuf, vbuf, 0, cbuf);
+    left_tcol_coef_kernel<<<1, 256, 0, st>>>(Tm, m, m - 1, beta, dbuf, vbuf, 0, cbuf, 0);
     RHQR_LAUNCH_CHECK();
     left_scale_last_kernel<T><<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(U, ldu, n, m - 1, gam, scaling == 0);
     RHQR_LAUNCH_CHECK();
@@ -421,6 +428,227 @@ rhqr_status left_factor(const SketchView &s, const void *W, int32_t wt, int64_t 
   if (wt == RHQR_F32)
     return left_typed<float>(s, (const float *)W, n, m, ldw, scaling, (float *)U, ldu, S, lds, T, R, (float *)Q,
                              ldq, ws, ws_bytes, info, st);
+  return RHQR_ENOTSUP;
+}
+
+// ---------------------------------------------------------------------------
+// blockRHQR (Algorithm 5): the columns in blocks of bs.  Block j is refreshed
+// with every earlier block k in turn,
+//   Y = Psi W^(j),  C = T^(k)t S^(k)t Y,  W^(j) <- W^(j) - U^(k) C,
+// its rows above the block are R's off-diagonal block (they are no longer
+// changed), and Algorithm 4 factors it with the global Psi and the global
+// column indices, using only the block's own reflectors (lo = first column).
+// ---------------------------------------------------------------------------
+
+// C = T_k^t (S_k^t Y) for the kb reflectors of an earlier block starting at
+// column k0 (S_k: p x kb, column l vanishing above row k0 + l; T_k: its kb x kb
+// upper-triangular diagonal block of T, ld ldt) and the nb columns of Y
+// (p x nb, ldy).  C is kb x nb, column-major.  One CTA per column of Y.
+__global__ void block_coef_kernel(const double *Sk, int64_t lds, int64_t p, int32_t k0, const double *Tk,
+                                  int32_t ldt, int32_t kb, const double *Y, int64_t ldy, double *C) {
+  __shared__ double m1[1024];
+  const int c = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double *y = Y + (int64_t)c * ldy;
+  for (int l = wid; l < kb; l += nw) {
+    const double *sl = Sk + (int64_t)l * lds;
+    double acc = 0.0;
+    for (int64_t r = k0 + l + lane; r < p; r += 32) acc += sl[r] * y[r];
+    acc = warp_sum(acc);
+    if (lane == 0) m1[l] = acc;
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < kb; l += blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i <= l; ++i) acc += Tk[(int64_t)l * ldt + i] * m1[i];
+    C[(int64_t)c * kb + l] = acc;
+  }
+}
+
+// Wb[i, c] -= sum_l Uk[i, l] C(l, c) for every row i (one row per thread,
+// grid-stride): each row of U_k and of the block is read once and the block's
+// row written once; C (kb x nb <= 64 x 64) sits in shared memory.
+constexpr int kMaxBlockCols = 64;
+template <class T, int NB>
+__global__ void __launch_bounds__(256) block_update_kernel(const T *Uk, int64_t ldu, int32_t kb, const double *C,
+                                                           T *Wb, int64_t ldw, int32_t nb, int64_t n) {
+  __shared__ T Cs[kMaxBlockCols * NB];  // Cs[l * NB + c], zero for c >= nb
+  for (int e = threadIdx.x; e < kb * NB; e += blockDim.x) {
+    const int l = e / NB, c = e - l * NB;
+    Cs[e] = c < nb ? (T)C[(int64_t)c * kb + l] : T(0);
+  }
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T acc[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) acc[c] = c < nb ? Wb[(int64_t)c * ldw + i] : T(0);
+    for (int l = 0; l < kb; ++l) {
+      const T u = Uk[(int64_t)l * ldu + i];
+      const T *cl = Cs + l * NB;
+#pragma unroll
+      for (int c = 0; c < NB; ++c) acc[c] -= u * cl[c];
+    }
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      if (c < nb) Wb[(int64_t)c * ldw + i] = acc[c];
+  }
+}
+
+template <class T>
+static rhqr_status block_update(const T *Uk, int64_t ldu, int32_t kb, const double *C, T *Wb, int64_t ldw,
+                                int32_t nb, int64_t n, cudaStream_t st) {
+  const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
+  if (nb <= 16) block_update_kernel<T, 16><<<grid, 256, 0, st>>>(Uk, ldu, kb, C, Wb, ldw, nb, n);
+  else if (nb <= 32) block_update_kernel<T, 32><<<grid, 256, 0, st>>>(Uk, ldu, kb, C, Wb, ldw, nb, n);
+  else block_update_kernel<T, 64><<<grid, 256, 0, st>>>(Uk, ldu, kb, C, Wb, ldw, nb, n);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
+}
+
+size_t block_workspace_bytes(const SketchView &s, int64_t n, int32_t m, int32_t bs, int32_t wt) {
+  Carver c(nullptr, 0);
+  c.take<char>(left_workspace_bytes(s, n, m, wt));
+  c.take<double>((size_t)kMaxBlockCols * kMaxBlockCols);  // C
+  c.take<double>((size_t)m * m);                          // S^t S scratch of the Woodbury T
+  (void)bs;
+  return c.used() + 1024;
+}
+
+template <class T>
+static rhqr_status block_typed(const SketchView &s, const T *W, int64_t n, int32_t m, int64_t ldw, int32_t bs,
+                               int32_t scaling, T *U, int64_t ldu, double *S, int64_t lds, double *Tm, double *R,
+                               T *Q, int64_t ldq, void *ws, size_t ws_bytes, rhqr_info *info, cudaStream_t st) {
+  const int64_t p = (int64_t)s.k + m;
+  const int32_t wt = sizeof(T) == 8 ? RHQR_F64 : RHQR_F32;
+  Carver cv(ws, ws_bytes);
+  double *Zraw = cv.take<double>((size_t)p * m);
+  double *y = cv.take<double>(p);
+  double *cbuf = cv.take<double>(m);
+  double *vbuf = cv.take<double>(m);
+  double *dbuf = cv.take<double>(m);
+  double *gam = cv.take<double>(m);
+  double *beta = cv.take<double>(m);
+  int *stop = cv.take<int>(4);
+  double *Gm = cv.take<double>((size_t)m * m);
+  char *GT = cv.take<char>(small_padded_bytes(m));
+  void *stage = nullptr;
+  if (s.kind == RHQR_SKETCH_SRHT) stage = cv.take<char>((size_t)s.N1 * s.d2 * sizeof(T));
+  else stage = cv.take<double>((size_t)ceil_div(n, LG_RB) * s.k);
+  const size_t apply_ws = sketch_apply_workspace_bytes(s, m, wt, n, m);
+  char *aws = cv.take<char>(apply_ws);
+  double *Cb = cv.take<double>((size_t)kMaxBlockCols * kMaxBlockCols);
+  double *SS = cv.take<double>((size_t)m * m);
+  if (cv.overflow()) return RHQR_ENOMEM;
+  if (m > 1024 || bs < 1 || bs > kMaxBlockCols) return RHQR_ENOTSUP;
+
+  RHQR_CUDA_TRY(cudaMemsetAsync(stop, 0, 4 * sizeof(int), st));
+  RHQR_CUDA_TRY(cudaMemsetAsync(Tm, 0, sizeof(double) * m * m, st));
+  // the blocks are refreshed in place in U
+  RHQR_CUDA_TRY(cudaMemcpy2DAsync(U, (size_t)ldu * sizeof(T), W, (size_t)ldw * sizeof(T), (size_t)n * sizeof(T),
+                                  (size_t)m, cudaMemcpyDeviceToDevice, st));
+  const double scale = 1.0 / sqrt((double)s.k);
+  const unsigned upd_grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
+  ColArgs ca{U, ldu, U, ldu, n, m, 0, cbuf, gam, y, scaling == 0 ? 1 : 0, 0};
+  for (int32_t c0 = 0; c0 < m; c0 += bs) {
+    const int32_t c1 = std::min(m, c0 + bs), nb = c1 - c0;
+    T *Wb = U + (int64_t)c0 * ldu;
+    double *Zb = Zraw + (int64_t)c0 * p;
+    // refresh with each earlier block in turn, re-sketching the block every time
+    for (int32_t k0 = 0; k0 < c0; k0 += bs) {
+      const int32_t kb = std::min(bs, c0 - k0);
+      RHQR_TRY(sketch_apply_simt(s, m, Wb, wt, n, nb, ldu, Zb, p, aws, apply_ws, st));
+      block_coef_kernel<<<(unsigned)nb, 256, 0, st>>>(S + (int64_t)k0 * lds, lds, p, k0, Tm + (int64_t)k0 * m + k0, m,
+                                                      kb, Zb, p, Cb);
+      RHQR_LAUNCH_CHECK();
+      RHQR_TRY(block_update<T>(U + (int64_t)k0 * ldu, ldu, kb, Cb, Wb, ldu, nb, n, st));
+    }
+    // Algorithm 4 on the refreshed block: raw sketches first
+    RHQR_TRY(sketch_apply_simt(s, m, Wb, wt, n, nb, ldu, Zb, p, aws, apply_ws, st));
+    ca.lo = c0;
+    for (int32_t j = c0; j < c1; ++j) {
+      if (j > c0) {
+        dim3 g((unsigned)(j - c0), 2);
+        left_dots_kernel<<<g, 256, 0, st>>>(S, lds, p, j - 1, j - 1 - c0, Zraw + (int64_t)j * p, j - c0, dbuf, vbuf,
+                                            c0);
+        RHQR_LAUNCH_CHECK();
+        left_tcol_coef_kernel<<<1, 256, 0, st>>>(Tm, m, j - 1, beta, dbuf, vbuf, j - c0, cbuf, c0);
+        RHQR_LAUNCH_CHECK();
+      }
+      ca.j = j;
+      if (s.kind == RHQR_SKETCH_SRHT) {
+        left_refresh_kernel<T><<<upd_grid, 256, 0, st>>>(ca);
+        RHQR_LAUNCH_CHECK();
+        size_t smem = (size_t)s.N2 * sizeof(T);
+        if (smem > 48 * 1024)
+          RHQR_CUDA_TRY(cudaFuncSetAttribute(left_column_srht_kernel<T, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        left_column_srht_kernel<T, true><<<s.N1, 512, smem, st>>>(ca, s.sign_bits, s.N2, s.i2_list, s.d2, (T *)stage);
+        RHQR_LAUNCH_CHECK();
+        left_srht_combine_kernel<T><<<(unsigned)ceil_div(s.k, 128), 128, 0, st>>>(
+            (const T *)stage, s.N1, s.d2, s.sample_i1, s.sample_slot, s.k, m, scale, y);
+        RHQR_LAUNCH_CHECK();
+      } else {
+        const int nbk = (int)ceil_div(n, LG_RB);
+        switch (s.omega_dtype) {
+          case RHQR_F64:
+            left_column_gauss_kernel<T, double><<<nbk, LG_RB, 0, st>>>(ca, (const double *)s.G, s.ldg, s.k,
+                                                                       (double *)stage);
+            break;
+          case RHQR_F32:
+            left_column_gauss_kernel<T, float><<<nbk, LG_RB, 0, st>>>(ca, (const float *)s.G, s.ldg, s.k,
+                                                                      (double *)stage);
+            break;
+          case RHQR_BF16:
+            left_column_gauss_kernel<T, __nv_bfloat16><<<nbk, LG_RB, 0, st>>>(ca, (const __nv_bfloat16 *)s.G, s.ldg,
+                                                                              s.k, (double *)stage);
+            break;
+          case RHQR_F16:
+            left_column_gauss_kernel<T, __half><<<nbk, LG_RB, 0, st>>>(ca, (const __half *)s.G, s.ldg, s.k,
+                                                                       (double *)stage);
+            break;
+          default:
+            return RHQR_EINVAL;
+        }
+        RHQR_LAUNCH_CHECK();
+        left_gauss_reduce_kernel<<<(unsigned)ceil_div(s.k, 128), 128, 0, st>>>((const double *)stage, nbk, s.k, m,
+                                                                               scale, y);
+        RHQR_LAUNCH_CHECK();
+      }
+      left_rhvector_kernel<T><<<1, 256, 0, st>>>(y, p, m, j, scaling, S, lds, R, beta, gam, U, ldu, info, stop);
+      RHQR_LAUNCH_CHECK();
+    }
+    // finish the block's T (its last column) and the last column's deferred scale
+    {
+      dim3 g((unsigned)std::max(1, nb - 1), 2);
+      left_dots_kernel<<<g, 256, 0, st>>>(S, lds, p, c1 - 1, nb - 1, Zraw, 0, dbuf, vbuf, c0);
+      RHQR_LAUNCH_CHECK();
+      left_tcol_coef_kernel<<<1, 256, 0, st>>>(Tm, m, c1 - 1, beta, dbuf, vbuf, 0, cbuf, c0);
+      RHQR_LAUNCH_CHECK();
+      left_scale_last_kernel<T><<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(U, ldu, n, c1 - 1, gam, scaling == 0);
+      RHQR_LAUNCH_CHECK();
+    }
+  }
+  // the compact form of all m reflectors: T^{-1} = sut(S^t S) + diag(1 / beta)
+  // (eq. generalwoodburry); its diagonal blocks are the blocks' T^(j)
+  RHQR_TRY(t_factor_small(S, lds, p, m, beta, SS, Tm, st));
+  if (Q != nullptr) {
+    RHQR_TRY(t_u1t(Tm, S, lds, m, Gm, st));
+    RHQR_TRY(pad_transpose<T>(Gm, m, 1, (T *)GT, st));
+    RHQR_TRY(rows_form_q<T>(U, ldu, 0, n, m, (const T *)GT, Q, ldq, st));
+  }
+  return RHQR_OK;
+}
+
+rhqr_status block_factor(const SketchView &s, const void *W, int32_t wt, int64_t n, int32_t m, int64_t ldw,
+                         int32_t bs, int32_t scaling, void *U, int64_t ldu, double *S, int64_t lds, double *T,
+                         double *R, void *Q, int64_t ldq, void *ws, size_t ws_bytes, rhqr_info *info,
+                         cudaStream_t st) {
+  if (wt == RHQR_F64)
+    return block_typed<double>(s, (const double *)W, n, m, ldw, bs, scaling, (double *)U, ldu, S, lds, T, R,
+                               (double *)Q, ldq, ws, ws_bytes, info, st);
+  if (wt == RHQR_F32)
+    return block_typed<float>(s, (const float *)W, n, m, ldw, bs, scaling, (float *)U, ldu, S, lds, T, R, (float *)Q,
+                              ldq, ws, ws_bytes, info, st);
   return RHQR_ENOTSUP;
 }
 
@@ -506,7 +734,7 @@ static rhqr_status arnoldi_reflect(ArnoldiState &a, const T *w, double *h, rhqr_
   const int64_t p = (int64_t)a.view.k + M;
   // the column kernel reads W[J * ldw + i]: present w as column J of a virtual matrix
   const T *Wbase = w - (int64_t)J * a.n;
-  ColArgs ca{Wbase, a.n, a.U, a.ldu, a.n, M, J, a.c, a.gamma, a.y, a.scaling == 0 ? 1 : 0};
+  ColArgs ca{Wbase, a.n, a.U, a.ldu, a.n, M, J, a.c, a.gamma, a.y, a.scaling == 0 ? 1 : 0, 0};
   const double scale = 1.0 / sqrt((double)a.view.k);
   if (a.view.kind == RHQR_SKETCH_SRHT) {
     left_refresh_kernel<T><<<(unsigned)std::min<int64_t>(ceil_div(a.n, 256), 152 * 8), 256, 0, st>>>(ca);
@@ -553,9 +781,9 @@ static rhqr_status arnoldi_reflect(ArnoldiState &a, const T *w, double *h, rhqr_
   // column J of T: t_J = (-beta T_J S_J^t s_J; beta)
   {
     dim3 g((unsigned)std::max(1, J), 2);
-    left_dots_kernel<<<g, 256, 0, st>>>(a.S, a.lds, p, J, J, a.z, 0, a.d, a.v);
+    left_dots_kernel<<<g, 256, 0, st>>>(a.S, a.lds, p, J, J, a.z, 0, a.d, a.v, 0);
     RHQR_LAUNCH_CHECK();
-    left_tcol_coef_kernel<<<1, 256, 0, st>>>(a.T, M, J, a.beta, a.d, a.v, 0, a.c);
+    left_tcol_coef_kernel<<<1, 256, 0, st>>>(a.T, M, J, a.beta, a.d, a.v, 0, a.c, 0);
     RHQR_LAUNCH_CHECK();
   }
   a.j = J + 1;
@@ -592,9 +820,9 @@ static rhqr_status arnoldi_step_t(ArnoldiState &a, const T *w, double *h, T *qn,
   RHQR_TRY(sketch_apply_simt(a.view, a.M, w, sizeof(T) == 8 ? RHQR_F64 : RHQR_F32, a.n, 1, a.n, a.z, p, a.aws,
                              a.aws_bytes, st));
   dim3 g((unsigned)J, 2);
-  left_dots_kernel<<<g, 256, 0, st>>>(a.S, a.lds, p, 0, 0, a.z, J, a.d, a.v);
+  left_dots_kernel<<<g, 256, 0, st>>>(a.S, a.lds, p, 0, 0, a.z, J, a.d, a.v, 0);
   RHQR_LAUNCH_CHECK();
-  left_tcol_coef_kernel<<<1, 256, 0, st>>>(a.T, a.M, -1, a.beta, a.d, a.v, J, a.c);
+  left_tcol_coef_kernel<<<1, 256, 0, st>>>(a.T, a.M, -1, a.beta, a.d, a.v, J, a.c, 0);
   RHQR_LAUNCH_CHECK();
   RHQR_TRY(arnoldi_reflect<T>(a, w, h, info, st));
   if (qn != nullptr) RHQR_TRY(arnoldi_basis<T>(a, qn, st));

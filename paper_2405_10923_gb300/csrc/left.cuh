@@ -11,6 +11,15 @@ rhqr_status left_factor(const SketchView &s, const void *W, int32_t wt, int64_t 
                         int32_t scaling, void *U, int64_t ldu, double *S, int64_t lds, double *T, double *R, void *Q,
                         int64_t ldq, void *ws, size_t ws_bytes, rhqr_info *info, cudaStream_t st);
 
+// blockRHQR (Algorithm 5) with blocks of bs columns (1 <= bs <= 64); outputs
+// as left_factor, with T the compact-form T of all m reflectors (its diagonal
+// blocks are the blocks' T^(j)).
+size_t block_workspace_bytes(const SketchView &s, int64_t n, int32_t m, int32_t bs, int32_t wt);
+rhqr_status block_factor(const SketchView &s, const void *W, int32_t wt, int64_t n, int32_t m, int64_t ldw,
+                         int32_t bs, int32_t scaling, void *U, int64_t ldu, double *S, int64_t lds, double *T,
+                         double *R, void *Q, int64_t ldq, void *ws, size_t ws_bytes, rhqr_info *info,
+                         cudaStream_t st);
+
 // State of one RHQR-Arnoldi process (Algorithm 7): M = mmax + 1 reflectors in
 // compact form (U n x M in the basis dtype, S = Psi U, T), Psi = diag(I_M, Omega).
 struct ArnoldiState {

@@ -99,7 +99,7 @@ rhqr_status rhqr_pipeline_create(rhqr_sketch s, int32_t wt, int64_t n, int32_t m
   if (sk < m) return RHQR_EINVAL;
   size_t ws_bytes = 0;
   RHQR_TRY(rhqr_workspace_size(s, n, m, wt, &o, &ws_bytes));
-  const bool want_U = o.want_U || o.alg == RHQR_ALG_LEFT;
+  const bool want_U = o.want_U || o.alg != RHQR_ALG_REC;
 
   rhqr_pipeline_s *p = new (std::nothrow) rhqr_pipeline_s();
   if (p == nullptr) return RHQR_ENOMEM;

@@ -295,6 +295,39 @@ rhqr_status copy_f64(const double *A, int64_t n, double *B, cudaStream_t st) {
   return RHQR_OK;
 }
 
+// Column equilibration of a sketch: d_j = ||Z[:, j]||_2 (1 for a zero column),
+// Z[:, j] /= d_j.  One CTA per column, fixed-order sum.
+__global__ void equilibrate_columns_kernel(double *Z, int64_t ldz, int64_t p, double *d) {
+  __shared__ double red[32];
+  double *z = Z + (int64_t)blockIdx.x * ldz;
+  double acc = 0.0;
+  for (int64_t r = threadIdx.x; r < p; r += blockDim.x) acc += z[r] * z[r];
+  acc = block_sum(acc, red);
+  const double nrm = acc > 0.0 ? sqrt(acc) : 1.0;
+  for (int64_t r = threadIdx.x; r < p; r += blockDim.x) z[r] = z[r] / nrm;
+  if (threadIdx.x == 0) d[blockIdx.x] = nrm;
+}
+
+// A[:, j] *= d_j (A rows x m, ld lda)
+__global__ void scale_columns_kernel(double *A, int64_t lda, int64_t rows, int32_t m, const double *d) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * m) return;
+  const int64_t j = e / rows, i = e - j * rows;
+  A[j * lda + i] *= d[j];
+}
+
+rhqr_status equilibrate_columns(double *Z, int64_t ldz, int64_t p, int32_t m, double *d, cudaStream_t st) {
+  equilibrate_columns_kernel<<<(unsigned)m, 256, 0, st>>>(Z, ldz, p, d);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
+}
+
+rhqr_status scale_columns(double *A, int64_t lda, int64_t rows, int32_t m, const double *d, cudaStream_t st) {
+  scale_columns_kernel<<<(unsigned)ceil_div(rows * m, 256), 256, 0, st>>>(A, lda, rows, m, d);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
+}
+
 rhqr_status info_passes(rhqr_info *info, int32_t passes, cudaStream_t st) {
   info_pass_kernel<<<1, 32, 0, st>>>(info, passes);
   RHQR_LAUNCH_CHECK();

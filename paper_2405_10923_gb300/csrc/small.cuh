@@ -31,5 +31,10 @@ rhqr_status m_factor(const double *T, const double *S, int64_t lds, const double
 rhqr_status cast_f32(const double *A, int64_t n, float *B, cudaStream_t st);
 rhqr_status copy_f64(const double *A, int64_t n, double *B, cudaStream_t st);
 rhqr_status info_passes(rhqr_info *info, int32_t passes, cudaStream_t st);
+// Column equilibration of a sketch (Z[:, j] /= d_j = ||Z[:, j]||) and the
+// column scaling A[:, j] *= d_j that undoes it (on R after the Householder QR,
+// on Z itself).
+rhqr_status equilibrate_columns(double *Z, int64_t ldz, int64_t p, int32_t m, double *d, cudaStream_t st);
+rhqr_status scale_columns(double *A, int64_t lda, int64_t rows, int32_t m, const double *d, cudaStream_t st);
 
 }  // namespace rhqr

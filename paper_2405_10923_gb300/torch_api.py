@@ -59,10 +59,11 @@ class Sketch:
 
 
 def make_opts(alg=ALG_REC, passes=1, limbs_first=2, limbs_refine=2, want_U=False, want_Q=True, scaling=0,
-              wait_budget=0, solve=0):
+              wait_budget=0, solve=0, block_size=32, column_scaling=0):
     o = rhqr_default_opts()
     o.alg, o.passes, o.limbs_first, o.limbs_refine = alg, passes, limbs_first, limbs_refine
     o.want_U, o.want_Q, o.scaling, o.wait_budget, o.solve = int(want_U), int(want_Q), scaling, wait_budget, solve
+    o.block_size, o.column_scaling = block_size, int(column_scaling)
     return o
 
 
@@ -91,7 +92,7 @@ def factor(sk: Sketch, W: torch.Tensor, opts=None, out=None, ws: Workspace | Non
     n, m = W.shape
     opts = opts or make_opts(**kw)
     wt = dtype_code(W)
-    want_U = bool(opts.want_U) or opts.alg == ALG_LEFT
+    want_U = bool(opts.want_U) or opts.alg != ALG_REC
     if out is None:
         out = factor_outputs(sk, n, m, W.dtype, want_U, bool(opts.want_Q), W.device)
     need = rhqr_workspace_size(sk.handle, n, m, wt, opts)
