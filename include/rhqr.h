@@ -325,6 +325,38 @@ rhqr_status rhqr_blas2_rgs(rhqr_sketch s, const void *W, int32_t wt, int64_t n, 
                            rhqr_stream_t stream);
 
 /*
+ * rhqr_trim_factor -- left-looking trimRHQR (Section 7): W (n x m, dtype wt =
+ * F64 or F32) = H(u_1, Omega, 1) ... H(u_m, Omega, m) [R; 0] with the modified
+ * randomized reflectors H(u, Omega, j) = I - beta u (Omega u)^t [0 Omega_{j:n}]
+ * (eq. rhousebisbis), Omega = Omega_full of the sketch (k x n, no exact top
+ * block).  The sketch size k may be smaller than m.  The method needs unit
+ * first m columns of Omega: the SRHT has them; for a Gaussian sketch the first
+ * m columns of Omega_full are normalised (Omega' = Omega_full with columns
+ * 0..m-1 divided by their norms), and every sketch is taken with Omega'.
+ * Column j is refreshed as w_j <- w_j - U Tt^t ut((Omega U)^t Omega) w_j
+ * (eq. trimrhqrcompactfact), then trimRHVector takes u_j.
+ * Outputs (device):
+ *   U  : n x m, dtype wt, ldu >= n (unit diagonal, or ||Omega u_j|| = sqrt 2
+ *        with scaling = 1)
+ *   S  : k x m float64, lds >= k   (= Omega' U)
+ *   T  : m x m float64 (right-wise products, eq. Tqdefbis):
+ *        H_1 ... H_m = I - U T ut((Omega U)^t Omega)
+ *   Tt : m x m float64 (left-wise products, eq. Sqdefbis):
+ *        H_m ... H_1 = I - U Tt^t ut((Omega U)^t Omega)
+ *   R  : m x m float64;  Q : n x m, dtype wt, ldq >= n, or NULL
+ *        (Q = [I_m; 0] - U T ut(S^t Omega'_{:, 0:m}))
+ *   info : device rhqr_info (breakdown: Omega' w' = 0)
+ * ws/ws_bytes : device workspace of at least rhqr_trim_workspace bytes.
+ * Requires 1 <= m <= 1024, n > m, and for the Gaussian kind n equal to the
+ * sketch's n (else RHQR_EINVAL).
+ */
+rhqr_status rhqr_trim_workspace(rhqr_sketch s, int32_t wt, int64_t n, int32_t m, size_t *bytes);
+rhqr_status rhqr_trim_factor(rhqr_sketch s, const void *W, int32_t wt, int64_t n, int32_t m, int64_t ldw,
+                             int32_t scaling, void *U, int64_t ldu, double *S, int64_t lds, double *T, double *Tt,
+                             double *R, void *Q, int64_t ldq, void *ws, size_t ws_bytes, rhqr_info *info,
+                             rhqr_stream_t stream);
+
+/*
  * Factorisation stream for matrices held in host memory (no counterpart in the
  * paper, which factors a matrix where the arithmetic runs).  Each submission
  * is one rhqr_factor (Algorithm 4 or 6, options as bound at create) of a host

@@ -99,6 +99,9 @@ _SIGNATURES = {
     "rhqr_sketch_apply_noalloc": (_i32, [_p, _i32, _p, _i32, _i64, _i32, _i64, _p, _i64, _p]),
     "rhqr_arnoldi_solution": (_i32, [_p, _p, _i64, _i32, _p, _p, _p, _p, _p, _p]),
     "rhqr_blas2_rgs_workspace": (_i32, [_p, _i32, _i64, _i32, ctypes.POINTER(_sz)]),
+    "rhqr_trim_workspace": (_i32, [_p, _i32, _i64, _i32, ctypes.POINTER(_sz)]),
+    "rhqr_trim_factor": (_i32, [_p, _p, _i32, _i64, _i32, _i64, _i32, _p, _i64, _p, _i64, _p, _p, _p, _p, _i64, _p, _sz,
+                                _p, _p]),
     "rhqr_blas2_rgs": (_i32, [_p, _p, _i32, _i64, _i32, _i64, _p, _i64, _p, _p, _p, _p, _sz, _p, _p]),
     "rhqr_batch_create": (_i32, [_i32, _p, _p, _i32, _p, _p, _p, ctypes.POINTER(rhqr_opts), _p, _p, _p, _p, _p, _p,
                                  ctypes.POINTER(_p)]),
@@ -300,6 +303,19 @@ def rhqr_blas2_rgs_workspace(s, wt, n, m) -> int:
 def rhqr_blas2_rgs(s, W, wt, n, m, ldw, Q, ldq, R, T, S, ws, ws_bytes, info, stream=None) -> None:
     _check("rhqr_blas2_rgs", load().rhqr_blas2_rgs(s, _ptr(W), wt, n, m, ldw, _ptr(Q), ldq, _ptr(R), _ptr(T), _ptr(S),
                                                    _ptr(ws), ws_bytes, _ptr(info), _stream(stream)))
+
+
+def rhqr_trim_workspace(s, wt, n, m) -> int:
+    out = _sz()
+    _check("rhqr_trim_workspace", load().rhqr_trim_workspace(s, wt, n, m, ctypes.byref(out)))
+    return out.value
+
+
+def rhqr_trim_factor(s, W, wt, n, m, ldw, scaling, U, ldu, S, lds, T, Tt, R, Q, ldq, ws, ws_bytes, info,
+                     stream=None) -> None:
+    _check("rhqr_trim_factor", load().rhqr_trim_factor(s, _ptr(W), wt, n, m, ldw, scaling, _ptr(U), ldu, _ptr(S), lds,
+                                                       _ptr(T), _ptr(Tt), _ptr(R), _ptr(Q), ldq, _ptr(ws), ws_bytes,
+                                                       _ptr(info), _stream(stream)))
 
 
 def rhqr_sketch_apply_noalloc(s, m, X, xt, n, c, ldx, Z, ldz, stream=None) -> None:

@@ -13,6 +13,7 @@
 //   4. RHVector (Algorithm 2) on (w_j, y): sigma, rho, gamma, beta, s_j, r_j
 //   5. t_j = (-beta T_j S_j^t s_j; beta) and the next step's coefficients.
 #include "apply.cuh"
+#include "column.cuh"
 #include "common.cuh"
 #include "left.cuh"
 #include "small.cuh"
@@ -72,175 +73,6 @@ __global__ void left_tcol_coef_kernel(double *T, int32_t m, int32_t j, const dou
 }
 
 // ---------------------------------------------------------------------------
-// step 2: column kernels
-// ---------------------------------------------------------------------------
-struct ColArgs {
-  const void *W;
-  int64_t ldw;
-  void *U;
-  int64_t ldu;
-  int64_t n;
-  int32_t m, j;
-  const double *c;      // j coefficients
-  const double *gamma;  // gamma[j-1] scales column j-1
-  double *y;            // (k+m) sketch, rows < m written here
-  int32_t unit;         // unit-diagonal scaling: u_jj = 1 exactly
-  int32_t lo;           // first column of the block whose reflectors refresh column j (0: all)
-};
-
-template <class T>
-__device__ __forceinline__ T refresh_row(const ColArgs &a, int64_t i, const double *c_s, T inv_g) {
-  const T *W = (const T *)a.W;
-  T *U = (T *)a.U;
-  T w = W[(int64_t)a.j * a.ldw + i];
-  const int j = a.j, lo = a.lo;
-  // previous columns of the block, the last one still unscaled
-  for (int l = lo; l + 1 < j; ++l) w -= U[(int64_t)l * a.ldu + i] * (T)c_s[l - lo];
-  if (j - 1 >= lo) {
-    T *up = U + (int64_t)(j - 1) * a.ldu + i;
-    T u = (i < j - 1) ? T(0) : ((i == j - 1 && a.unit) ? T(1) : *up * inv_g);
-    *up = u;
-    w -= u * (T)c_s[j - 1 - lo];
-  }
-  U[(int64_t)j * a.ldu + i] = w;
-  return w;
-}
-
-// Refresh of column j over all rows with the whole GPU (one row per thread,
-// grid-stride): w_j <- w_j - U_{j-1} c (the previous columns read with four
-// independent partial sums), the deferred scaling of column j-1, and the exact
-// top rows of the sketch.
-template <class T>
-__global__ void __launch_bounds__(256) left_refresh_kernel(ColArgs a) {
-  __shared__ double c_s[1024];
-  const int j = a.j, lo = a.lo;
-  for (int l = threadIdx.x; l < j - lo; l += blockDim.x) c_s[l] = a.c[l];
-  const T inv_g = (j - 1 >= lo) ? (T)(1.0 / a.gamma[j - 1]) : T(1);
-  __syncthreads();
-  const T *W = (const T *)a.W;
-  T *U = (T *)a.U;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-    T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
-    int l = lo;
-    for (; l + 4 < j; l += 4) {
-      p0 += U[(int64_t)l * a.ldu + i] * (T)c_s[l - lo];
-      p1 += U[(int64_t)(l + 1) * a.ldu + i] * (T)c_s[l + 1 - lo];
-      p2 += U[(int64_t)(l + 2) * a.ldu + i] * (T)c_s[l + 2 - lo];
-      p3 += U[(int64_t)(l + 3) * a.ldu + i] * (T)c_s[l + 3 - lo];
-    }
-    for (; l + 1 < j; ++l) p0 += U[(int64_t)l * a.ldu + i] * (T)c_s[l - lo];
-    T w = W[(int64_t)j * a.ldw + i] - ((p0 + p1) + (p2 + p3));
-    if (j - 1 >= lo) {
-      T *up = U + (int64_t)(j - 1) * a.ldu + i;
-      const T u = (i < j - 1) ? T(0) : ((i == j - 1 && a.unit) ? T(1) : *up * inv_g);
-      *up = u;
-      w -= u * (T)c_s[j - 1 - lo];
-    }
-    U[(int64_t)j * a.ldu + i] = w;
-    if (i < a.m) a.y[i] = (double)w;
-  }
-}
-
-// SRHT: block j1 owns rows [j1 N2, (j1+1) N2); refresh (or read the refreshed
-// column), signs, FWHT, keep samples
-template <class T, bool REFRESHED>
-__global__ void left_column_srht_kernel(ColArgs a, const uint32_t *sign_bits, int32_t N2, const int32_t *i2_list,
-                                        int32_t d2, T *Ystage) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *v = reinterpret_cast<T *>(smem_raw);
-  __shared__ double c_s[1024];
-  for (int l = threadIdx.x; l < a.j - a.lo; l += blockDim.x) c_s[l] = a.c[l];
-  const T inv_g = (a.j - 1 >= a.lo) ? (T)(1.0 / a.gamma[a.j - 1]) : T(1);
-  __syncthreads();
-  const int64_t row0 = (int64_t)blockIdx.x * N2;
-  for (int t = threadIdx.x; t < N2; t += blockDim.x) {
-    int64_t i = row0 + t;
-    T val = T(0);
-    if (i < a.n) {
-      if (REFRESHED) {
-        if (i >= a.m) {
-          const T w = ((const T *)a.U)[(int64_t)a.j * a.ldu + i];
-          val = ((sign_bits[i >> 5] >> (i & 31)) & 1u) ? -w : w;
-        }
-      } else {
-        T w = refresh_row<T>(a, i, c_s, inv_g);
-        if (i < a.m) {
-          a.y[i] = (double)w;
-        } else {
-          val = ((sign_bits[i >> 5] >> (i & 31)) & 1u) ? -w : w;
-        }
-      }
-    }
-    v[t] = val;
-  }
-  __syncthreads();
-  for (int h = 1; h < N2; h <<= 1) {
-    for (int t = threadIdx.x; t < (N2 >> 1); t += blockDim.x) {
-      int i = (t / h) * (2 * h) + (t % h);
-      T x0 = v[i], x1 = v[i + h];
-      v[i] = x0 + x1;
-      v[i + h] = x0 - x1;
-    }
-    __syncthreads();
-  }
-  T *ys = Ystage + (int64_t)blockIdx.x * d2;
-  for (int s = threadIdx.x; s < d2; s += blockDim.x) ys[s] = v[i2_list[s]];
-}
-
-template <class T>
-__global__ void left_srht_combine_kernel(const T *Ystage, int32_t N1, int32_t d2, const int32_t *sample_i1,
-                                         const int32_t *sample_slot, int32_t k, int32_t m, double scale, double *y) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= k) return;
-  int i1 = sample_i1[r], slot = sample_slot[r];
-  double acc = 0.0;
-  for (int j1 = 0; j1 < N1; ++j1) {
-    double t = (double)Ystage[(int64_t)j1 * d2 + slot];
-    acc += (__popc(i1 & j1) & 1) ? -t : t;
-  }
-  y[m + r] = acc * scale;
-}
-
-// Gaussian: block owns rows [b*RB, (b+1)*RB); partial[b][r] = sum_i G[r, i] w_i over rows i >= m
-constexpr int LG_RB = 256;
-template <class T, class TG>
-__global__ void __launch_bounds__(LG_RB) left_column_gauss_kernel(ColArgs a, const TG *G, int64_t ldg, int32_t k,
-                                                                  double *part) {
-  __shared__ double w_s[LG_RB];
-  __shared__ double c_s[1024];
-  for (int l = threadIdx.x; l < a.j - a.lo; l += blockDim.x) c_s[l] = a.c[l];
-  const T inv_g = (a.j - 1 >= a.lo) ? (T)(1.0 / a.gamma[a.j - 1]) : T(1);
-  __syncthreads();
-  const int64_t row0 = (int64_t)blockIdx.x * LG_RB;
-  int64_t i = row0 + threadIdx.x;
-  double wd = 0.0;
-  if (i < a.n) {
-    T w = refresh_row<T>(a, i, c_s, inv_g);
-    if (i < a.m) a.y[i] = (double)w;
-    else wd = (double)w;
-  }
-  w_s[threadIdx.x] = wd;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = LG_RB / 32;
-  const int64_t rows = min((int64_t)LG_RB, a.n - row0);
-  for (int r = wid; r < k; r += nw) {
-    double acc = 0.0;
-    for (int t = lane; t < rows; t += 32) acc += to_f64<TG>(G[(int64_t)r * ldg + row0 + t]) * w_s[t];
-    acc = warp_sum(acc);
-    if (lane == 0) part[(int64_t)blockIdx.x * k + r] = acc;
-  }
-}
-
-__global__ void left_gauss_reduce_kernel(const double *part, int32_t nb, int32_t k, int32_t m, double scale,
-                                         double *y) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= k) return;
-  double acc = 0.0;
-  for (int b = 0; b < nb; ++b) acc += part[(int64_t)b * k + r];
-  y[m + r] = acc * scale;
-}
-
-// ---------------------------------------------------------------------------
 // step 4: RHVector on y (Algorithm 2), one block
 // ---------------------------------------------------------------------------
 template <class T>
@@ -284,16 +116,6 @@ __global__ void left_rhvector_kernel(const double *y, int64_t p, int32_t m, int3
     beta[j] = (scaling == 0) ? 1.0 + fabs(a) / rho : 1.0;
     gamma_out[j] = div;
   }
-}
-
-// final deferred scale of column j: u = u~ / gamma (rows >= j+1), u_j = 1 (or gamma/div)
-template <class T>
-__global__ void left_scale_last_kernel(T *U, int64_t ldu, int64_t n, int32_t j, const double *gamma, int32_t unit) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  T *up = U + (int64_t)j * ldu + i;
-  T inv_g = (T)(1.0 / gamma[j]);
-  *up = (i < j) ? T(0) : ((i == j && unit) ? T(1) : *up * inv_g);
 }
 
 // ---------------------------------------------------------------------------
@@ -345,7 +167,7 @@ static rhqr_status left_typed(const SketchView &s, const T *W, int64_t n, int32_
   // raw sketches of all columns (Algorithm 4 sketches w_j before refreshing it)
   RHQR_TRY(sketch_apply_simt(s, m, W, sizeof(T) == 8 ? RHQR_F64 : RHQR_F32, n, m, ldw, Zraw, p, aws, apply_ws, st));
 
-  ColArgs ca{W, ldw, U, ldu, n, m, 0, cbuf, gam, y, scaling == 0 ? 1 : 0, 0};
+  ColArgs ca{W, ldw, U, ldu, n, m, 0, cbuf, gam, y, scaling == 0 ? 1 : 0, 0, m};
   const double scale = 1.0 / sqrt((double)s.k);
   for (int j = 0; j < m; ++j) {
     if (j >= 1) {
@@ -548,7 +370,7 @@ static rhqr_status block_typed(const SketchView &s, const T *W, int64_t n, int32
                                   (size_t)m, cudaMemcpyDeviceToDevice, st));
   const double scale = 1.0 / sqrt((double)s.k);
   const unsigned upd_grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
-  ColArgs ca{U, ldu, U, ldu, n, m, 0, cbuf, gam, y, scaling == 0 ? 1 : 0, 0};
+  ColArgs ca{U, ldu, U, ldu, n, m, 0, cbuf, gam, y, scaling == 0 ? 1 : 0, 0, m};
   for (int32_t c0 = 0; c0 < m; c0 += bs) {
     const int32_t c1 = std::min(m, c0 + bs), nb = c1 - c0;
     T *Wb = U + (int64_t)c0 * ldu;
@@ -734,7 +556,7 @@ static rhqr_status arnoldi_reflect(ArnoldiState &a, const T *w, double *h, rhqr_
   const int64_t p = (int64_t)a.view.k + M;
   // the column kernel reads W[J * ldw + i]: present w as column J of a virtual matrix
   const T *Wbase = w - (int64_t)J * a.n;
-  ColArgs ca{Wbase, a.n, a.U, a.ldu, a.n, M, J, a.c, a.gamma, a.y, a.scaling == 0 ? 1 : 0, 0};
+  ColArgs ca{Wbase, a.n, a.U, a.ldu, a.n, M, J, a.c, a.gamma, a.y, a.scaling == 0 ? 1 : 0, 0, M};
   const double scale = 1.0 / sqrt((double)a.view.k);
   if (a.view.kind == RHQR_SKETCH_SRHT) {
     left_refresh_kernel<T><<<(unsigned)std::min<int64_t>(ceil_div(a.n, 256), 152 * 8), 256, 0, st>>>(ca);

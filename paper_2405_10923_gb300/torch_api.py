@@ -13,11 +13,12 @@ from . import (ALG_LEFT, ALG_REC, BF16, F16, F32, F64, GAUSSIAN, SRHT, colmajor,
                rhqr_batch_create, rhqr_batch_destroy, rhqr_batch_get_tuning, rhqr_batch_set_tuning, rhqr_batch_tune,
                rhqr_batch_workspace_size, rhqr_factor_batched, rhqr_arnoldi_begin, rhqr_arnoldi_create, rhqr_arnoldi_destroy, rhqr_arnoldi_export, rhqr_arnoldi_step,
                rhqr_default_opts, rhqr_factor, rhqr_pipeline_create, rhqr_pipeline_destroy, rhqr_pipeline_submit,
-               rhqr_pipeline_wait, rhqr_arnoldi_solution, rhqr_blas2_rgs, rhqr_blas2_rgs_workspace, rhqr_reconstruct, rhqr_sketch_apply, rhqr_sketch_apply_workspace,
+               rhqr_pipeline_wait, rhqr_arnoldi_solution, rhqr_blas2_rgs, rhqr_blas2_rgs_workspace, rhqr_reconstruct,
+               rhqr_trim_factor, rhqr_trim_workspace, rhqr_sketch_apply, rhqr_sketch_apply_workspace,
                rhqr_sketch_create, rhqr_sketch_destroy, rhqr_sketch_export, rhqr_sketch_shape, rhqr_workspace_size)
 
 TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}
-__all__ = ["Sketch", "Arnoldi", "GMRES", "Batch", "Pipeline", "factor", "reconstruct", "colmajor", "ALG_LEFT", "ALG_REC", "GAUSSIAN", "SRHT"]
+__all__ = ["Sketch", "Arnoldi", "GMRES", "Batch", "Pipeline", "factor", "trim_factor", "reconstruct", "colmajor", "ALG_LEFT", "ALG_REC", "GAUSSIAN", "SRHT"]
 
 
 class Sketch:
@@ -155,6 +156,30 @@ def blas2_rgs(sk: Sketch, W: torch.Tensor):
     ws = torch.empty(max(need, 1), dtype=torch.uint8, device=W.device)
     rhqr_blas2_rgs(sk.handle, W, wt, n, m, ld_of(W), Q, ld_of(Q), R, T, S, ws, need, info)
     return Q, R, T, S, info
+
+
+def trim_factor(sk: Sketch, W: torch.Tensor, scaling: int = 0, want_Q: bool = True):
+    """rhqr_trim_factor (left-looking trimRHQR, Section 7) on a column-major W;
+    returns a dict with U, S (k x m), T, Tt, R, Q (or None) and info."""
+    n, m = W.shape
+    wt = dtype_code(W)
+    dev = W.device
+    out = {
+        "U": colmajor(torch.zeros((n, m), dtype=W.dtype, device=dev)),
+        "S": colmajor(torch.zeros((sk.k, m), dtype=torch.float64, device=dev)),
+        "T": colmajor(torch.zeros((m, m), dtype=torch.float64, device=dev)),
+        "Tt": colmajor(torch.zeros((m, m), dtype=torch.float64, device=dev)),
+        "R": colmajor(torch.zeros((m, m), dtype=torch.float64, device=dev)),
+        "Q": colmajor(torch.zeros((n, m), dtype=W.dtype, device=dev)) if want_Q else None,
+        "info": torch.zeros(4, dtype=torch.int32, device=dev),
+    }
+    need = rhqr_trim_workspace(sk.handle, wt, n, m)
+    ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    Q = out["Q"]
+    rhqr_trim_factor(sk.handle, W, wt, n, m, ld_of(W), scaling, out["U"], ld_of(out["U"]), out["S"], ld_of(out["S"]),
+                     out["T"], out["Tt"], out["R"], Q, ld_of(Q) if Q is not None else n, ws, need, out["info"])
+    out["ws"] = ws
+    return out
 
 
 def reconstruct(sk: Sketch, S, T, R, Z, W, want_Q=True):

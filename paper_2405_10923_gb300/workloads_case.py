@@ -18,7 +18,7 @@ warm-up, inputs resident on the device):
                 100, float64, up to --cycles cycles towards 1e-8 (time per cycle
                 and the relative residual after each)
 
-python -m paper_2405_10923_gb300.workloads_case [--cases left_small srht_left srht_block srht_rec rgs arnoldi gmres] [--reps 3]
+python -m paper_2405_10923_gb300.workloads_case [--cases left_small srht_left srht_block srht_trim srht_rec rgs arnoldi gmres] [--reps 3]
 
 Accuracy is reported with the library's own sketch of the result in float64
 (orth = max |eig(I - (Psi Q)^t Psi Q)|) and resid = ||W - QR||_F / ||W||_F
@@ -50,7 +50,7 @@ def _time(fn, reps):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--cases", nargs="+", default=["left_small", "srht_left", "srht_block", "srht_rec", "rgs", "arnoldi", "gmres"])
+    ap.add_argument("--cases", nargs="+", default=["left_small", "srht_left", "srht_block", "srht_trim", "srht_rec", "rgs", "arnoldi", "gmres"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--cycles", type=int, default=5)
     a = ap.parse_args()
@@ -90,7 +90,7 @@ def main():
 
     n, m, k = 1 << 20, 128, 512
     W64 = None
-    if any(c in a.cases for c in ("srht_left", "srht_rec", "rgs", "srht_block")):
+    if any(c in a.cases for c in ("srht_left", "srht_rec", "rgs", "srht_block", "srht_trim")):
         W64 = ri.device_spectrum(n, m, 1e12, 1002, dtype=torch.float64)
         W32 = ri.device_spectrum(n, m, 1e12, 1002, dtype=torch.float32)
         sk = ta.Sketch(n, k, rh.SRHT, 2002)
@@ -114,6 +114,20 @@ def main():
                 es = W.element_size()
                 emit(case="srht_block", path=f"blockRHQR {name}, blocks of {bs}", n=n, m=m, k=k, sketch="srht",
                      ms=ms, gbps_w_factored=n * m * es / (ms * 1e-3) / 1e9, orth=orth, resid=resid)
+    if "srht_trim" in a.cases:
+        for kt in (k, 96):  # the sketch size of the other cases, and fewer rows than columns
+            skt = ta.Sketch(n, kt, rh.SRHT, 2002)
+            for W, name in ((W64, "f64"), (W32, "f32")):
+                out = ta.trim_factor(skt, W)
+                ms = _time(lambda: ta.trim_factor(skt, W), a.reps)
+                Q, R = out["Q"], out["R"]
+                W64c = W.double()
+                resid = float(torch.linalg.norm(W64c - Q.double() @ R) / torch.linalg.norm(W64c))
+                sv = torch.linalg.svdvals(Q.double())
+                emit(case="srht_trim", path=f"trimRHQR left-looking {name}", n=n, m=m, k=kt, sketch="srht", ms=ms,
+                     gbps_w_factored=n * m * W.element_size() / (ms * 1e-3) / 1e9, resid=resid,
+                     cond_q=float(sv[0] / sv[-1]), status=ta.read_info(out["info"])["status"])
+            skt.close()
     if "srht_rec" in a.cases:
         for W, name, passes in ((W64, "f64", 2), (W32, "f32", 3)):
             opts = ta.make_opts(alg=rh.ALG_REC, passes=passes)
