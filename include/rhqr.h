@@ -226,10 +226,21 @@ rhqr_status rhqr_reconstruct(rhqr_sketch s, const double *S, int64_t lds, const 
  *            NULL) and writes the number of reflectors taken to *count (host).
  * Breakdown (rho = 0) and non-finite values are reported in the device info.
  * Work is enqueued on `stream`; a handle serves one stream at a time.
+ *
+ * create_batch: nrhs independent processes (one per right-hand side, 1 ..
+ * 65535) sharing the sketch; every kernel of begin, step and solution is
+ * launched once for all of them.  The device arrays of the calls then hold
+ * one column per process: r0, w, q1, q_next, x0, x are n x nrhs (ld n); h0, h
+ * are (mmax+1) x nrhs (ld mmax+1); info holds nrhs records; export writes
+ * nrhs stacked blocks (U + b ldu (mmax+1), S + b lds (mmax+1), T + b
+ * (mmax+1)^2); solution reads H + b ldh mmax and writes y + b mmax, res + b.
+ * rhqr_arnoldi_create is create_batch with nrhs = 1.
  */
 typedef struct rhqr_arnoldi_s *rhqr_arnoldi;
 rhqr_status rhqr_arnoldi_create(rhqr_sketch s, int64_t n, int32_t mmax, int32_t basis_dtype, int32_t scaling,
                                 rhqr_arnoldi *out);
+rhqr_status rhqr_arnoldi_create_batch(rhqr_sketch s, int64_t n, int32_t mmax, int32_t nrhs, int32_t basis_dtype,
+                                      int32_t scaling, rhqr_arnoldi *out);
 rhqr_status rhqr_arnoldi_destroy(rhqr_arnoldi a);
 rhqr_status rhqr_arnoldi_begin(rhqr_arnoldi a, const void *r0, double *h0, void *q1, rhqr_info *info,
                                rhqr_stream_t stream);
@@ -256,6 +267,12 @@ rhqr_status rhqr_arnoldi_export(rhqr_arnoldi a, void *U, int64_t ldu, double *S,
  */
 rhqr_status rhqr_arnoldi_solution(rhqr_arnoldi a, const double *H, int64_t ldh, int32_t m, const double *h0,
                                   const void *x0, void *x, double *y, double *res, rhqr_stream_t stream);
+/* The same with x0 and x in dtype xdt (F64 or F32) independent of the basis
+ * dtype: a float32 basis can update a float64 iterate (the restart residual
+ * is then formed in float64, e.g. by rhqr_stencil_residual). */
+rhqr_status rhqr_arnoldi_solution_x(rhqr_arnoldi a, const double *H, int64_t ldh, int32_t m, const double *h0,
+                                    const void *x0, void *x, int32_t xdt, double *y, double *res,
+                                    rhqr_stream_t stream);
 
 /*
  * Batched recRHQR (Algorithm 6 with the refinement passes of rhqr_factor) of
@@ -323,6 +340,27 @@ rhqr_status rhqr_blas2_rgs_workspace(rhqr_sketch s, int32_t wt, int64_t n, int32
 rhqr_status rhqr_blas2_rgs(rhqr_sketch s, const void *W, int32_t wt, int64_t n, int32_t m, int64_t ldw, void *Q,
                            int64_t ldq, double *R, double *T, double *S, void *ws, size_t ws_bytes, rhqr_info *info,
                            rhqr_stream_t stream);
+
+/*
+ * Operator of the RHQR-GMRES workload (not part of the method): the 2-D
+ * convection-diffusion operator -Laplace(u) + pe (u_x + u_y) on the unit
+ * square with zero Dirichlet boundary, g x g interior points (n = g^2, row
+ * r = iy g + ix), h = 1/(g+1), central differences, scaled by h^2:
+ *   (A u)_r = 4 u_r - (1 + c) u_{r-1} - (1 - c) u_{r+1} - (1 + c) u_{r-g}
+ *             - (1 - c) u_{r+g},   c = pe h / 2  (neighbours off the grid are 0).
+ * rhqr_stencil_apply: Y = A X for nrhs columns (X, Y: n x nrhs, ld n, dtype
+ *   F64 or F32; Y must not overlap X).
+ * rhqr_stencil_residual: R = B - A X formed in float64 and stored in dtype
+ *   rdt (F64 or F32: the Krylov basis may be narrower than B and X), and
+ *   norms[2b] = ||B[:, b] - A X[:, b]||_2, norms[2b+1] = ||B[:, b]||_2 of the
+ *   float64 values (fixed-order sums) -- the restart residual of GMRES.
+ *   work: rhqr_stencil_residual_workspace bytes.
+ */
+rhqr_status rhqr_stencil_apply(int32_t g, double pe, const void *X, int32_t dt, int32_t nrhs, void *Y,
+                               rhqr_stream_t stream);
+rhqr_status rhqr_stencil_residual_workspace(int32_t g, int32_t nrhs, size_t *bytes);
+rhqr_status rhqr_stencil_residual(int32_t g, double pe, const void *B, const void *X, int32_t dt, int32_t nrhs, void *R,
+                                  int32_t rdt, double *norms, void *work, size_t work_bytes, rhqr_stream_t stream);
 
 /*
  * rhqr_trim_factor -- left-looking trimRHQR (Section 7): W (n x m, dtype wt =

@@ -92,6 +92,11 @@ _SIGNATURES = {
     "rhqr_reconstruct": (_i32, [_p, _p, _i64, _p, _p, _p, _i64, _p, _i32, _i64, _i32, _i64, _p, _i64, _p, _i64, _p,
                                 _sz, _p]),
     "rhqr_arnoldi_create": (_i32, [_p, _i64, _i32, _i32, _i32, ctypes.POINTER(_p)]),
+    "rhqr_arnoldi_create_batch": (_i32, [_p, _i64, _i32, _i32, _i32, _i32, ctypes.POINTER(_p)]),
+    "rhqr_stencil_apply": (_i32, [_i32, ctypes.c_double, _p, _i32, _i32, _p, _p]),
+    "rhqr_stencil_residual_workspace": (_i32, [_i32, _i32, ctypes.POINTER(_sz)]),
+    "rhqr_stencil_residual": (_i32, [_i32, ctypes.c_double, _p, _p, _i32, _i32, _p, _i32, _p, _p, _sz, _p]),
+    "rhqr_arnoldi_solution_x": (_i32, [_p, _p, _i64, _i32, _p, _p, _p, _i32, _p, _p, _p]),
     "rhqr_arnoldi_destroy": (_i32, [_p]),
     "rhqr_arnoldi_begin": (_i32, [_p, _p, _p, _p, _p, _p]),
     "rhqr_arnoldi_step": (_i32, [_p, _p, _p, _p, _p, _p]),
@@ -268,6 +273,34 @@ def rhqr_arnoldi_create(s: int, n: int, mmax: int, basis_dtype: int = F64, scali
     return out.value
 
 
+def rhqr_arnoldi_create_batch(s: int, n: int, mmax: int, nrhs: int, basis_dtype: int = F64, scaling: int = 0) -> int:
+    out = _p()
+    _check("rhqr_arnoldi_create_batch",
+           load().rhqr_arnoldi_create_batch(s, n, mmax, nrhs, basis_dtype, scaling, ctypes.byref(out)))
+    return out.value
+
+
+def rhqr_stencil_apply(g, pe, X, dt, nrhs, Y, stream=None) -> None:
+    _check("rhqr_stencil_apply", load().rhqr_stencil_apply(g, pe, _ptr(X), dt, nrhs, _ptr(Y), _stream(stream)))
+
+
+def rhqr_stencil_residual_workspace(g, nrhs) -> int:
+    out = _sz()
+    _check("rhqr_stencil_residual_workspace", load().rhqr_stencil_residual_workspace(g, nrhs, ctypes.byref(out)))
+    return out.value
+
+
+def rhqr_stencil_residual(g, pe, B, X, dt, nrhs, R, rdt, norms, work, work_bytes, stream=None) -> None:
+    _check("rhqr_stencil_residual", load().rhqr_stencil_residual(g, pe, _ptr(B), _ptr(X), dt, nrhs, _ptr(R), rdt,
+                                                                 _ptr(norms), _ptr(work), work_bytes,
+                                                                 _stream(stream)))
+
+
+def rhqr_arnoldi_solution_x(a, H, ldh, m, h0, x0, x, xdt, y, res, stream=None) -> None:
+    _check("rhqr_arnoldi_solution_x", load().rhqr_arnoldi_solution_x(a, _ptr(H), ldh, m, _ptr(h0), _ptr(x0), _ptr(x),
+                                                                     xdt, _ptr(y), _ptr(res), _stream(stream)))
+
+
 def rhqr_arnoldi_destroy(a: int) -> None:
     _check("rhqr_arnoldi_destroy", load().rhqr_arnoldi_destroy(a))
 
@@ -422,6 +455,9 @@ def rhqr_profile_read() -> dict:
 
 
 def read_info(info_tensor) -> dict:
-    """Decode a 4-int32 device tensor holding an rhqr_info (synchronises)."""
-    v = info_tensor.cpu().tolist()
+    """Decode a 4-int32 device tensor holding an rhqr_info (synchronises).  For
+    several records (an (r, 4) tensor) the first non-OK one is returned (the
+    first one when all are OK)."""
+    rows = info_tensor.reshape(-1, 4).cpu().tolist()
+    v = next((r for r in rows if r[0] != 0), rows[0])
     return {"status": int(v[0]), "column": int(v[1]), "passes_done": int(v[2])}

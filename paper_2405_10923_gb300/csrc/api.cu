@@ -550,11 +550,12 @@ rhqr_status rhqr_reconstruct(rhqr_sketch s, const double *S, int64_t lds, const 
 // RHQR-Arnoldi
 // ---------------------------------------------------------------------------
 
-rhqr_status rhqr_arnoldi_create(rhqr_sketch s, int64_t n, int32_t mmax, int32_t basis_dtype, int32_t scaling,
-                                rhqr_arnoldi *out) {
+rhqr_status rhqr_arnoldi_create_batch(rhqr_sketch s, int64_t n, int32_t mmax, int32_t nrhs, int32_t basis_dtype,
+                                      int32_t scaling, rhqr_arnoldi *out) {
   if (out == nullptr) return RHQR_EINVAL;
   *out = nullptr;
-  if (s == nullptr || mmax < 1 || !valid_dtype_hd(basis_dtype) || (scaling != 0 && scaling != 1))
+  if (s == nullptr || mmax < 1 || nrhs < 1 || nrhs > 65535 || !valid_dtype_hd(basis_dtype) ||
+      (scaling != 0 && scaling != 1))
     return RHQR_EINVAL;
   const int32_t M = mmax + 1;
   if (M > 1024) return RHQR_ENOTSUP;
@@ -567,7 +568,8 @@ rhqr_status rhqr_arnoldi_create(rhqr_sketch s, int64_t n, int32_t mmax, int32_t 
   a->st.dtype = basis_dtype;
   a->st.scaling = scaling;
   a->st.j = 0;
-  size_t bytes = arnoldi_state_bytes(s->view, n, M, basis_dtype);
+  a->st.nrhs = nrhs;
+  size_t bytes = arnoldi_state_bytes(s->view, n, M, basis_dtype, nrhs);
   if (cudaMalloc(&a->mem, bytes) != cudaSuccess) {
     (void)cudaGetLastError();
     delete a;
@@ -578,7 +580,7 @@ rhqr_status rhqr_arnoldi_create(rhqr_sketch s, int64_t n, int32_t mmax, int32_t 
     delete a;
     return RHQR_ENOMEM;
   }
-  if (cudaMalloc((void **)&a->lsq, sizeof(double) * arnoldi_solution_scratch_doubles(M)) != cudaSuccess) {
+  if (cudaMalloc((void **)&a->lsq, sizeof(double) * arnoldi_solution_scratch_doubles(M, nrhs)) != cudaSuccess) {
     (void)cudaGetLastError();
     cudaFree(a->mem);
     delete a;
@@ -586,6 +588,11 @@ rhqr_status rhqr_arnoldi_create(rhqr_sketch s, int64_t n, int32_t mmax, int32_t 
   }
   *out = a;
   return RHQR_OK;
+}
+
+rhqr_status rhqr_arnoldi_create(rhqr_sketch s, int64_t n, int32_t mmax, int32_t basis_dtype, int32_t scaling,
+                                rhqr_arnoldi *out) {
+  return rhqr_arnoldi_create_batch(s, n, mmax, 1, basis_dtype, scaling, out);
 }
 
 rhqr_status rhqr_arnoldi_destroy(rhqr_arnoldi a) {
@@ -600,7 +607,7 @@ rhqr_status rhqr_arnoldi_begin(rhqr_arnoldi a, const void *r0, double *h0, void 
                                rhqr_stream_t stream) {
   if (a == nullptr || r0 == nullptr || h0 == nullptr || info == nullptr) return RHQR_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  RHQR_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(rhqr_info), st));
+  RHQR_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(rhqr_info) * a->st.nrhs, st));
   return arnoldi_begin(a->st, r0, h0, q1, info, st);
 }
 
@@ -611,11 +618,18 @@ rhqr_status rhqr_arnoldi_step(rhqr_arnoldi a, const void *w, double *h, void *q_
   return arnoldi_step(a->st, w, h, q_next, info, (cudaStream_t)stream);
 }
 
-rhqr_status rhqr_arnoldi_solution(rhqr_arnoldi a, const double *H, int64_t ldh, int32_t m, const double *h0,
-                                  const void *x0, void *x, double *y, double *res, rhqr_stream_t stream) {
+rhqr_status rhqr_arnoldi_solution_x(rhqr_arnoldi a, const double *H, int64_t ldh, int32_t m, const double *h0,
+                                    const void *x0, void *x, int32_t xdt, double *y, double *res,
+                                    rhqr_stream_t stream) {
   if (a == nullptr || H == nullptr || h0 == nullptr || y == nullptr || res == nullptr) return RHQR_EINVAL;
   if (x != nullptr && x0 == nullptr) return RHQR_EINVAL;
-  return arnoldi_solution(a->st, a->lsq, H, ldh, m, h0, x0, x, y, res, (cudaStream_t)stream);
+  return arnoldi_solution(a->st, a->lsq, H, ldh, m, h0, x0, x, xdt, y, res, (cudaStream_t)stream);
+}
+
+rhqr_status rhqr_arnoldi_solution(rhqr_arnoldi a, const double *H, int64_t ldh, int32_t m, const double *h0,
+                                  const void *x0, void *x, double *y, double *res, rhqr_stream_t stream) {
+  if (a == nullptr) return RHQR_EINVAL;
+  return rhqr_arnoldi_solution_x(a, H, ldh, m, h0, x0, x, a->st.dtype, y, res, stream);
 }
 
 rhqr_status rhqr_arnoldi_export(rhqr_arnoldi a, void *U, int64_t ldu, double *S, int64_t lds, double *T,
@@ -625,17 +639,20 @@ rhqr_status rhqr_arnoldi_export(rhqr_arnoldi a, void *U, int64_t ldu, double *S,
   const ArnoldiState &A = a->st;
   const int64_t p = (int64_t)A.view.k + A.M;
   size_t es = dtype_size(A.dtype);
+  const int32_t B = A.nrhs;
   if (U != nullptr) {
     if (ldu < A.n) return RHQR_EINVAL;
-    RHQR_CUDA_TRY(cudaMemcpy2DAsync(U, ldu * es, A.U, A.ldu * es, A.n * es, A.M, cudaMemcpyDeviceToDevice, st));
+    RHQR_CUDA_TRY(cudaMemcpy2DAsync(U, ldu * es, A.U, A.ldu * es, A.n * es, (size_t)A.M * B, cudaMemcpyDeviceToDevice,
+                                    st));
     RHQR_TRY(arnoldi_scale_copy(A, U, ldu, st));
   }
   if (S != nullptr) {
     if (lds < p) return RHQR_EINVAL;
-    RHQR_CUDA_TRY(cudaMemcpy2DAsync(S, lds * 8, A.S, A.lds * 8, p * 8, A.M, cudaMemcpyDeviceToDevice, st));
+    RHQR_CUDA_TRY(
+        cudaMemcpy2DAsync(S, lds * 8, A.S, A.lds * 8, p * 8, (size_t)A.M * B, cudaMemcpyDeviceToDevice, st));
   }
   if (T != nullptr)
-    RHQR_CUDA_TRY(cudaMemcpyAsync(T, A.T, sizeof(double) * A.M * A.M, cudaMemcpyDeviceToDevice, st));
+    RHQR_CUDA_TRY(cudaMemcpyAsync(T, A.T, sizeof(double) * A.M * A.M * B, cudaMemcpyDeviceToDevice, st));
   if (count != nullptr) *count = A.j;
   return RHQR_OK;
 }

@@ -12,6 +12,17 @@ namespace rhqr {
 // ---------------------------------------------------------------------------
 // step 2: column kernels
 // ---------------------------------------------------------------------------
+// Element strides between the problems of a batch of same-shape independent
+// problems (the RHQR-Arnoldi processes of several right-hand sides): a kernel
+// launched with gridDim.y = batch count works on problem blockIdx.y.  All zero
+// for a single problem.
+struct Batch {
+  int64_t W, U;      // input column(s), reflector matrix (elements of the data type)
+  int64_t vec;       // per-problem vectors of length M (coefficients, gamma, beta, ...)
+  int64_t y;         // sketch vectors
+  int64_t stage;     // transform / partial-product staging
+};
+
 struct ColArgs {
   const void *W;
   int64_t ldw;
@@ -25,7 +36,21 @@ struct ColArgs {
   int32_t unit;         // unit-diagonal scaling: u_jj = 1 exactly
   int32_t lo;           // first column of the block whose reflectors refresh column j (0: all)
   int32_t skm;          // leading rows left out of the sketch: m for Psi_m = diag(I_m, Omega), 0 for Omega_full
+  Batch bt;             // batch strides (zero for one problem)
 };
+
+// The arguments of problem blockIdx.y of a batch.
+template <class T>
+__device__ __forceinline__ ColArgs batch_args(const ColArgs &a0) {
+  ColArgs a = a0;
+  const int64_t b = blockIdx.y;
+  a.W = (const T *)a0.W + b * a0.bt.W;
+  a.U = (T *)a0.U + b * a0.bt.U;
+  a.c = a0.c + b * a0.bt.vec;
+  a.gamma = a0.gamma + b * a0.bt.vec;
+  a.y = a0.y + b * a0.bt.y;
+  return a;
+}
 
 template <class T>
 __device__ __forceinline__ T refresh_row(const ColArgs &a, int64_t i, const double *c_s, T inv_g) {
@@ -50,7 +75,8 @@ __device__ __forceinline__ T refresh_row(const ColArgs &a, int64_t i, const doub
 // independent partial sums), the deferred scaling of column j-1, and the exact
 // top rows of the sketch.
 template <class T>
-__global__ void __launch_bounds__(256) left_refresh_kernel(ColArgs a) {
+__global__ void __launch_bounds__(256) left_refresh_kernel(ColArgs a0) {
+  const ColArgs a = batch_args<T>(a0);
   __shared__ double c_s[1024];
   const int j = a.j, lo = a.lo;
   for (int l = threadIdx.x; l < j - lo; l += blockDim.x) c_s[l] = a.c[l];
@@ -83,8 +109,10 @@ __global__ void __launch_bounds__(256) left_refresh_kernel(ColArgs a) {
 // SRHT: block j1 owns rows [j1 N2, (j1+1) N2); refresh (or read the refreshed
 // column), signs, FWHT, keep samples
 template <class T, bool REFRESHED>
-__global__ void left_column_srht_kernel(ColArgs a, const uint32_t *sign_bits, int32_t N2, const int32_t *i2_list,
+__global__ void left_column_srht_kernel(ColArgs a0, const uint32_t *sign_bits, int32_t N2, const int32_t *i2_list,
                                         int32_t d2, T *Ystage) {
+  const ColArgs a = batch_args<T>(a0);
+  Ystage += (int64_t)blockIdx.y * a0.bt.stage;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *v = reinterpret_cast<T *>(smem_raw);
   __shared__ double c_s[1024];
@@ -125,7 +153,10 @@ __global__ void left_column_srht_kernel(ColArgs a, const uint32_t *sign_bits, in
 
 template <class T>
 __global__ void left_srht_combine_kernel(const T *Ystage, int32_t N1, int32_t d2, const int32_t *sample_i1,
-                                         const int32_t *sample_slot, int32_t k, int32_t m, double scale, double *y) {
+                                         const int32_t *sample_slot, int32_t k, int32_t m, double scale, double *y,
+                                         int64_t bs_stage = 0, int64_t bs_y = 0) {
+  Ystage += (int64_t)blockIdx.y * bs_stage;
+  y += (int64_t)blockIdx.y * bs_y;
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= k) return;
   int i1 = sample_i1[r], slot = sample_slot[r];
@@ -140,8 +171,10 @@ __global__ void left_srht_combine_kernel(const T *Ystage, int32_t N1, int32_t d2
 // Gaussian: block owns rows [b*RB, (b+1)*RB); partial[b][r] = sum_i G[r, i] w_i over rows i >= m
 constexpr int LG_RB = 256;
 template <class T, class TG>
-__global__ void __launch_bounds__(LG_RB) left_column_gauss_kernel(ColArgs a, const TG *G, int64_t ldg, int32_t k,
+__global__ void __launch_bounds__(LG_RB) left_column_gauss_kernel(ColArgs a0, const TG *G, int64_t ldg, int32_t k,
                                                                   double *part) {
+  const ColArgs a = batch_args<T>(a0);
+  part += (int64_t)blockIdx.y * a0.bt.stage;
   __shared__ double w_s[LG_RB];
   __shared__ double c_s[1024];
   for (int l = threadIdx.x; l < a.j - a.lo; l += blockDim.x) c_s[l] = a.c[l];
@@ -168,7 +201,9 @@ __global__ void __launch_bounds__(LG_RB) left_column_gauss_kernel(ColArgs a, con
 }
 
 static __global__ void left_gauss_reduce_kernel(const double *part, int32_t nb, int32_t k, int32_t m, double scale,
-                                         double *y) {
+                                                double *y, int64_t bs_stage = 0, int64_t bs_y = 0) {
+  part += (int64_t)blockIdx.y * bs_stage;
+  y += (int64_t)blockIdx.y * bs_y;
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= k) return;
   double acc = 0.0;
@@ -178,7 +213,10 @@ static __global__ void left_gauss_reduce_kernel(const double *part, int32_t nb, 
 
 // final deferred scale of column j: u = u~ / gamma (rows >= j+1), u_j = 1 (or gamma/div)
 template <class T>
-__global__ void left_scale_last_kernel(T *U, int64_t ldu, int64_t n, int32_t j, const double *gamma, int32_t unit) {
+__global__ void left_scale_last_kernel(T *U, int64_t ldu, int64_t n, int32_t j, const double *gamma, int32_t unit,
+                                       int64_t bs_U = 0, int64_t bs_vec = 0) {
+  U += (int64_t)blockIdx.y * bs_U;
+  gamma += (int64_t)blockIdx.y * bs_vec;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   T *up = U + (int64_t)j * ldu + i;

@@ -26,8 +26,13 @@ namespace rhqr {
 // columns): d[t] = S[:, l] . s_j (t < nd), v[t] = S[:, l] . z (t < nv)
 // ---------------------------------------------------------------------------
 __global__ void left_dots_kernel(const double *S, int64_t lds, int64_t p, int32_t j, int32_t nd, const double *z,
-                                 int32_t nv, double *d, double *v, int32_t lo) {
+                                 int32_t nv, double *d, double *v, int32_t lo, int64_t bs_S = 0, int64_t bs_z = 0,
+                                 int64_t bs_vec = 0) {
   __shared__ double red[32];
+  S += (int64_t)blockIdx.z * bs_S;  // problem blockIdx.z of a batch
+  z += (int64_t)blockIdx.z * bs_z;
+  d += (int64_t)blockIdx.z * bs_vec;
+  v += (int64_t)blockIdx.z * bs_vec;
   const int t = blockIdx.x;  // d[t], v[t] belong to column l = lo + t
   const int l = lo + t;
   int which = blockIdx.y;  // 0: d (against s_j), 1: v (against z)
@@ -49,7 +54,13 @@ __global__ void left_dots_kernel(const double *S, int64_t lds, int64_t p, int32_
 // zero, the block's T is a diagonal block), then c = T_blk^t v for the nc
 // block columns lo .. lo + nc - 1.
 __global__ void left_tcol_coef_kernel(double *T, int32_t m, int32_t j, const double *beta, const double *d,
-                                      const double *v, int32_t nc, double *c, int32_t lo) {
+                                      const double *v, int32_t nc, double *c, int32_t lo, int64_t bs_T = 0,
+                                      int64_t bs_vec = 0) {
+  T += (int64_t)blockIdx.x * bs_T;  // problem blockIdx.x of a batch (one block each)
+  beta += (int64_t)blockIdx.x * bs_vec;
+  d += (int64_t)blockIdx.x * bs_vec;
+  v += (int64_t)blockIdx.x * bs_vec;
+  c += (int64_t)blockIdx.x * bs_vec;
   if (j >= 0) {
     double bj = beta[j];
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -75,11 +86,27 @@ __global__ void left_tcol_coef_kernel(double *T, int32_t m, int32_t j, const dou
 // ---------------------------------------------------------------------------
 // step 4: RHVector on y (Algorithm 2), one block
 // ---------------------------------------------------------------------------
+// Batches: problem blockIdx.x (one block each), element strides bs_*.
+struct RhvBatch {
+  int64_t y, S, R, vec, U, stop;
+};
+
 template <class T>
 __global__ void left_rhvector_kernel(const double *y, int64_t p, int32_t m, int32_t j, int32_t scaling, double *S,
                                      int64_t lds, double *R, double *beta, double *gamma_out, T *U, int64_t ldu,
-                                     rhqr_info *info, int *stop) {
+                                     rhqr_info *info, int *stop, RhvBatch bb = RhvBatch{}) {
   __shared__ double red[32];
+  {
+    const int64_t b = blockIdx.x;
+    y += b * bb.y;
+    S += b * bb.S;
+    R += b * bb.R;
+    beta += b * bb.vec;
+    gamma_out += b * bb.vec;
+    U += b * bb.U;
+    stop += b * bb.stop;
+    if (info != nullptr) info += b;
+  }
   if (*stop) return;
   double s = 0.0;
   for (int64_t r = j + threadIdx.x; r < p; r += blockDim.x) s += y[r] * y[r];
@@ -475,26 +502,40 @@ rhqr_status block_factor(const SketchView &s, const void *W, int32_t wt, int64_t
 }
 
 // ---------------------------------------------------------------------------
-// RHQR-Arnoldi (Algorithm 7) on the same kernels
+// RHQR-Arnoldi (Algorithm 7) on the same kernels, for a batch of nrhs
+// independent processes (one per right-hand side) sharing the sketch: every
+// kernel of a step is launched once for the whole batch, the process index
+// taken from the grid, and each process's arrays lie at a fixed stride.
 // ---------------------------------------------------------------------------
 
 // coef_l = sum_{i >= l} T[l, i] S[j, i] for l <= j (x = T_{j+1} S_{j+1}^t e_j),
-// the last one divided by gamma_j (column j of U is stored unscaled).
+// the last one divided by gamma_j (column j of U is stored unscaled).  One
+// block per process.
 __global__ void arnoldi_coef_kernel(const double *T, int32_t M, const double *S, int64_t lds, int32_t j,
-                                    const double *gamma, int32_t unit, double *coef) {
+                                    const double *gamma, double *coef, int64_t bs_S) {
+  const int64_t b = blockIdx.x;
+  T += b * (int64_t)M * M;
+  S += b * bs_S;
+  gamma += b * M;
+  coef += b * M;
   for (int l = threadIdx.x; l <= j; l += blockDim.x) {
     double acc = 0.0;
     for (int i = l; i <= j; ++i) acc += T[(int64_t)i * M + l] * S[(int64_t)i * lds + j];
     if (l == j) acc = acc / gamma[j];
     coef[l] = acc;
   }
-  (void)unit;
 }
 
 // q = e_j - U[:, 0..j] coef over all n rows; column j of U is unscaled except
 // rows <= j (zeros above, gamma at j), so row j gives exactly 1 - coef_j gamma_j / gamma_j.
+// Process blockIdx.y; q of process b at q + b n.
 template <class T>
-__global__ void arnoldi_q_kernel(const T *U, int64_t ldu, int64_t n, int32_t j, const double *coef, T *q) {
+__global__ void arnoldi_q_kernel(const T *U, int64_t ldu, int64_t n, int32_t j, const double *coef, T *q,
+                                 int64_t bs_U, int32_t M) {
+  const int64_t b = blockIdx.y;
+  U += b * bs_U;
+  coef += b * M;
+  q += b * n;
   __shared__ double c_s[1024];
   for (int l = threadIdx.x; l <= j; l += blockDim.x) c_s[l] = coef[l];
   __syncthreads();
@@ -505,109 +546,121 @@ __global__ void arnoldi_q_kernel(const T *U, int64_t ldu, int64_t n, int32_t j, 
   q[i] = (T)acc;
 }
 
-size_t arnoldi_state_bytes(const SketchView &s, int64_t n, int32_t M, int32_t dt) {
+static int64_t arnoldi_stage_elems(const SketchView &s, int64_t n) {
+  return s.kind == RHQR_SKETCH_SRHT ? (int64_t)s.N1 * s.d2 : ceil_div(n, LG_RB) * s.k;
+}
+
+size_t arnoldi_state_bytes(const SketchView &s, int64_t n, int32_t M, int32_t dt, int32_t nrhs) {
   Carver c(nullptr, 0);
   const int64_t p = (int64_t)s.k + M;
-  c.take<char>((size_t)n * M * dtype_size(dt));  // U
-  c.take<double>((size_t)p * M);                  // S
-  c.take<double>((size_t)M * M);                  // T
-  c.take<double>(8 * (size_t)M + 2 * p);          // beta gamma c v d coef y z
-  c.take<int>(4);
-  if (s.kind == RHQR_SKETCH_SRHT) c.take<char>((size_t)s.N1 * s.d2 * dtype_size(dt));
-  else c.take<double>((size_t)ceil_div(n, LG_RB) * s.k);
-  c.take<char>(sketch_apply_workspace_bytes(s, M, dt, n, 1));
+  c.take<char>((size_t)n * M * dtype_size(dt) * nrhs);  // U
+  c.take<double>((size_t)p * M * nrhs);                  // S
+  c.take<double>((size_t)M * M * nrhs);                  // T
+  c.take<double>((6 * (size_t)M + 2 * p) * nrhs);        // beta gamma c v d coef; y z
+  c.take<int>(4 * (size_t)nrhs);
+  const size_t es = s.kind == RHQR_SKETCH_SRHT ? dtype_size(dt) : sizeof(double);
+  c.take<char>((size_t)arnoldi_stage_elems(s, n) * es * nrhs);
+  c.take<char>(sketch_apply_workspace_bytes(s, M, dt, n, nrhs));
   return c.used() + 1024;
 }
 
 rhqr_status arnoldi_carve(ArnoldiState &a, void *mem, size_t bytes) {
   Carver c(mem, bytes);
   const int64_t p = (int64_t)a.view.k + a.M;
-  a.U = c.take<char>((size_t)a.n * a.M * dtype_size(a.dtype));
+  const int32_t B = a.nrhs, M = a.M;
+  a.U = c.take<char>((size_t)a.n * M * dtype_size(a.dtype) * B);
   a.ldu = a.n;
-  a.S = c.take<double>((size_t)p * a.M);
+  a.S = c.take<double>((size_t)p * M * B);
   a.lds = p;
-  a.T = c.take<double>((size_t)a.M * a.M);
-  double *vecs = c.take<double>(8 * (size_t)a.M + 2 * p);
+  a.T = c.take<double>((size_t)M * M * B);
+  double *vecs = c.take<double>((6 * (size_t)M + 2 * p) * B);
   a.beta = vecs;
-  a.gamma = vecs + a.M;
-  a.c = vecs + 2 * a.M;
-  a.v = vecs + 3 * a.M;
-  a.d = vecs + 4 * a.M;
-  a.coef = vecs + 5 * a.M;
-  a.y = vecs + 8 * a.M;
-  a.z = vecs + 8 * a.M + p;
-  a.stop = c.take<int>(4);
-  if (a.view.kind == RHQR_SKETCH_SRHT) {
-    a.stage_bytes = (size_t)a.view.N1 * a.view.d2 * dtype_size(a.dtype);
-  } else {
-    a.stage_bytes = (size_t)ceil_div(a.n, LG_RB) * a.view.k * sizeof(double);
-  }
+  a.gamma = vecs + (size_t)M * B;
+  a.c = vecs + 2 * (size_t)M * B;
+  a.v = vecs + 3 * (size_t)M * B;
+  a.d = vecs + 4 * (size_t)M * B;
+  a.coef = vecs + 5 * (size_t)M * B;
+  a.y = vecs + 6 * (size_t)M * B;
+  a.z = a.y + (size_t)p * B;
+  a.stop = c.take<int>(4 * (size_t)B);
+  a.stage_elems = arnoldi_stage_elems(a.view, a.n);
+  const size_t es = a.view.kind == RHQR_SKETCH_SRHT ? dtype_size(a.dtype) : sizeof(double);
+  a.stage_bytes = (size_t)a.stage_elems * es * B;
   a.stage = c.take<char>(a.stage_bytes);
-  a.aws_bytes = sketch_apply_workspace_bytes(a.view, a.M, a.dtype, a.n, 1);
+  a.aws_bytes = sketch_apply_workspace_bytes(a.view, M, a.dtype, a.n, B);
   a.aws = c.take<char>(a.aws_bytes);
   return c.overflow() ? RHQR_ENOMEM : RHQR_OK;
 }
 
-// refresh `w` with the reflectors 0..J-1 (coefficients in a.c), store it as
-// column J of U, sketch it into a.y (fused), then take reflector J.
+// column J of T for every process: t_J = (-beta T_J S_J^t s_J; beta)
+static rhqr_status arnoldi_tcol(ArnoldiState &a, cudaStream_t st) {
+  const int32_t J = a.j, M = a.M, B = a.nrhs;
+  const int64_t p = (int64_t)a.view.k + M;
+  dim3 g((unsigned)std::max(1, J), 2, (unsigned)B);
+  left_dots_kernel<<<g, 256, 0, st>>>(a.S, a.lds, p, J, J, a.z, 0, a.d, a.v, 0, a.lds * M, p, M);
+  RHQR_LAUNCH_CHECK();
+  left_tcol_coef_kernel<<<(unsigned)B, 256, 0, st>>>(a.T, M, J, a.beta, a.d, a.v, 0, a.c, 0, (int64_t)M * M, M);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
+}
+
+// refresh `w` (n x nrhs) with the reflectors 0..J-1 (coefficients in a.c),
+// store it as column J of U, sketch it into a.y (fused), then take reflector J.
 template <class T>
 static rhqr_status arnoldi_reflect(ArnoldiState &a, const T *w, double *h, rhqr_info *info, cudaStream_t st) {
-  const int32_t J = a.j, M = a.M;
+  const int32_t J = a.j, M = a.M, B = a.nrhs;
   const int64_t p = (int64_t)a.view.k + M;
   // the column kernel reads W[J * ldw + i]: present w as column J of a virtual matrix
   const T *Wbase = w - (int64_t)J * a.n;
-  ColArgs ca{Wbase, a.n, a.U, a.ldu, a.n, M, J, a.c, a.gamma, a.y, a.scaling == 0 ? 1 : 0, 0, M};
+  ColArgs ca{Wbase, a.n, a.U, a.ldu, a.n, M, J, a.c, a.gamma, a.y, a.scaling == 0 ? 1 : 0, 0, M,
+             Batch{a.n, a.ldu * M, M, p, a.stage_elems}};
   const double scale = 1.0 / sqrt((double)a.view.k);
   if (a.view.kind == RHQR_SKETCH_SRHT) {
-    left_refresh_kernel<T><<<(unsigned)std::min<int64_t>(ceil_div(a.n, 256), 152 * 8), 256, 0, st>>>(ca);
+    dim3 gr((unsigned)std::min<int64_t>(ceil_div(a.n, 256), std::max<int64_t>(1, 152 * 8 / B)), (unsigned)B);
+    left_refresh_kernel<T><<<gr, 256, 0, st>>>(ca);
     RHQR_LAUNCH_CHECK();
     size_t smem = (size_t)a.view.N2 * sizeof(T);
     if (smem > 48 * 1024)
       RHQR_CUDA_TRY(cudaFuncSetAttribute(left_column_srht_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
-    left_column_srht_kernel<T, true><<<a.view.N1, 512, smem, st>>>(ca, a.view.sign_bits, a.view.N2,
-                                                                    a.view.i2_list, a.view.d2, (T *)a.stage);
+    left_column_srht_kernel<T, true><<<dim3((unsigned)a.view.N1, (unsigned)B), 512, smem, st>>>(
+        ca, a.view.sign_bits, a.view.N2, a.view.i2_list, a.view.d2, (T *)a.stage);
     RHQR_LAUNCH_CHECK();
-    left_srht_combine_kernel<T><<<(unsigned)ceil_div(a.view.k, 128), 128, 0, st>>>(
-        (const T *)a.stage, a.view.N1, a.view.d2, a.view.sample_i1, a.view.sample_slot, a.view.k, M, scale, a.y);
+    left_srht_combine_kernel<T><<<dim3((unsigned)ceil_div(a.view.k, 128), (unsigned)B), 128, 0, st>>>(
+        (const T *)a.stage, a.view.N1, a.view.d2, a.view.sample_i1, a.view.sample_slot, a.view.k, M, scale, a.y,
+        a.stage_elems, p);
     RHQR_LAUNCH_CHECK();
   } else {
-    int nb = (int)ceil_div(a.n, LG_RB);
+    const dim3 gg((unsigned)ceil_div(a.n, LG_RB), (unsigned)B);
     switch (a.view.omega_dtype) {
       case RHQR_F64:
-        left_column_gauss_kernel<T, double><<<nb, LG_RB, 0, st>>>(ca, (const double *)a.view.G, a.view.ldg, a.view.k,
+        left_column_gauss_kernel<T, double><<<gg, LG_RB, 0, st>>>(ca, (const double *)a.view.G, a.view.ldg, a.view.k,
                                                                   (double *)a.stage);
         break;
       case RHQR_F32:
-        left_column_gauss_kernel<T, float><<<nb, LG_RB, 0, st>>>(ca, (const float *)a.view.G, a.view.ldg, a.view.k,
+        left_column_gauss_kernel<T, float><<<gg, LG_RB, 0, st>>>(ca, (const float *)a.view.G, a.view.ldg, a.view.k,
                                                                  (double *)a.stage);
         break;
       case RHQR_BF16:
-        left_column_gauss_kernel<T, __nv_bfloat16><<<nb, LG_RB, 0, st>>>(
+        left_column_gauss_kernel<T, __nv_bfloat16><<<gg, LG_RB, 0, st>>>(
             ca, (const __nv_bfloat16 *)a.view.G, a.view.ldg, a.view.k, (double *)a.stage);
         break;
       default:
-        left_column_gauss_kernel<T, __half><<<nb, LG_RB, 0, st>>>(ca, (const __half *)a.view.G, a.view.ldg, a.view.k,
+        left_column_gauss_kernel<T, __half><<<gg, LG_RB, 0, st>>>(ca, (const __half *)a.view.G, a.view.ldg, a.view.k,
                                                                   (double *)a.stage);
         break;
     }
     RHQR_LAUNCH_CHECK();
-    left_gauss_reduce_kernel<<<(unsigned)ceil_div(a.view.k, 128), 128, 0, st>>>((const double *)a.stage, nb,
-                                                                               a.view.k, M, scale, a.y);
+    left_gauss_reduce_kernel<<<dim3((unsigned)ceil_div(a.view.k, 128), (unsigned)B), 128, 0, st>>>(
+        (const double *)a.stage, (int32_t)ceil_div(a.n, LG_RB), a.view.k, M, scale, a.y, a.stage_elems, p);
     RHQR_LAUNCH_CHECK();
   }
-  // RHVector at column J; its "R column" is the Hessenberg column h (M entries)
-  left_rhvector_kernel<T><<<1, 256, 0, st>>>(a.y, p, M, J, a.scaling, a.S, a.lds, h - (int64_t)J * M, a.beta,
-                                             a.gamma, (T *)a.U, a.ldu, info, a.stop);
+  // RHVector at column J; its "R column" is the Hessenberg column h (M entries per process)
+  RhvBatch bb{p, a.lds * M, M, M, a.ldu * M, 4};
+  left_rhvector_kernel<T><<<(unsigned)B, 256, 0, st>>>(a.y, p, M, J, a.scaling, a.S, a.lds, h - (int64_t)J * M,
+                                                       a.beta, a.gamma, (T *)a.U, a.ldu, info, a.stop, bb);
   RHQR_LAUNCH_CHECK();
-  // column J of T: t_J = (-beta T_J S_J^t s_J; beta)
-  {
-    dim3 g((unsigned)std::max(1, J), 2);
-    left_dots_kernel<<<g, 256, 0, st>>>(a.S, a.lds, p, J, J, a.z, 0, a.d, a.v, 0);
-    RHQR_LAUNCH_CHECK();
-    left_tcol_coef_kernel<<<1, 256, 0, st>>>(a.T, M, J, a.beta, a.d, a.v, 0, a.c, 0);
-    RHQR_LAUNCH_CHECK();
-  }
+  RHQR_TRY(arnoldi_tcol(a, st));
   a.j = J + 1;
   return RHQR_OK;
 }
@@ -615,10 +668,11 @@ static rhqr_status arnoldi_reflect(ArnoldiState &a, const T *w, double *h, rhqr_
 // q_J = e_J - U_{J+1} T_{J+1} S_{J+1}^t e_J  (J = the newest reflector)
 template <class T>
 static rhqr_status arnoldi_basis(ArnoldiState &a, T *q, cudaStream_t st) {
-  const int32_t J = a.j - 1;
-  arnoldi_coef_kernel<<<1, 256, 0, st>>>(a.T, a.M, a.S, a.lds, J, a.gamma, a.scaling == 0, a.coef);
+  const int32_t J = a.j - 1, B = a.nrhs;
+  arnoldi_coef_kernel<<<(unsigned)B, 256, 0, st>>>(a.T, a.M, a.S, a.lds, J, a.gamma, a.coef, a.lds * a.M);
   RHQR_LAUNCH_CHECK();
-  arnoldi_q_kernel<T><<<(unsigned)ceil_div(a.n, 256), 256, 0, st>>>((const T *)a.U, a.ldu, a.n, J, a.coef, q);
+  arnoldi_q_kernel<T><<<dim3((unsigned)ceil_div(a.n, 256), (unsigned)B), 256, 0, st>>>(
+      (const T *)a.U, a.ldu, a.n, J, a.coef, q, a.ldu * a.M, a.M);
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }
@@ -627,8 +681,8 @@ template <class T>
 static rhqr_status arnoldi_begin_t(ArnoldiState &a, const T *r0, double *h0, T *q1, rhqr_info *info,
                                    cudaStream_t st) {
   a.j = 0;
-  RHQR_CUDA_TRY(cudaMemsetAsync(a.stop, 0, 4 * sizeof(int), st));
-  RHQR_CUDA_TRY(cudaMemsetAsync(a.T, 0, sizeof(double) * a.M * a.M, st));
+  RHQR_CUDA_TRY(cudaMemsetAsync(a.stop, 0, 4 * sizeof(int) * a.nrhs, st));
+  RHQR_CUDA_TRY(cudaMemsetAsync(a.T, 0, sizeof(double) * a.M * a.M * a.nrhs, st));
   RHQR_TRY(arnoldi_reflect<T>(a, r0, h0, info, st));
   if (q1 != nullptr) RHQR_TRY(arnoldi_basis<T>(a, q1, st));
   return RHQR_OK;
@@ -636,15 +690,15 @@ static rhqr_status arnoldi_begin_t(ArnoldiState &a, const T *r0, double *h0, T *
 
 template <class T>
 static rhqr_status arnoldi_step_t(ArnoldiState &a, const T *w, double *h, T *qn, rhqr_info *info, cudaStream_t st) {
-  const int32_t J = a.j;
-  const int64_t p = (int64_t)a.view.k + a.M;
-  // z = Psi w (the sketch of A q_j), then c = T_J^t S_J^t z
-  RHQR_TRY(sketch_apply_simt(a.view, a.M, w, sizeof(T) == 8 ? RHQR_F64 : RHQR_F32, a.n, 1, a.n, a.z, p, a.aws,
+  const int32_t J = a.j, M = a.M, B = a.nrhs;
+  const int64_t p = (int64_t)a.view.k + M;
+  // z = Psi w (the sketches of A q_j of every process), then c = T_J^t S_J^t z
+  RHQR_TRY(sketch_apply_simt(a.view, M, w, sizeof(T) == 8 ? RHQR_F64 : RHQR_F32, a.n, B, a.n, a.z, p, a.aws,
                              a.aws_bytes, st));
-  dim3 g((unsigned)J, 2);
-  left_dots_kernel<<<g, 256, 0, st>>>(a.S, a.lds, p, 0, 0, a.z, J, a.d, a.v, 0);
+  dim3 g((unsigned)J, 2, (unsigned)B);
+  left_dots_kernel<<<g, 256, 0, st>>>(a.S, a.lds, p, 0, 0, a.z, J, a.d, a.v, 0, a.lds * M, p, M);
   RHQR_LAUNCH_CHECK();
-  left_tcol_coef_kernel<<<1, 256, 0, st>>>(a.T, a.M, -1, a.beta, a.d, a.v, J, a.c, 0);
+  left_tcol_coef_kernel<<<(unsigned)B, 256, 0, st>>>(a.T, M, -1, a.beta, a.d, a.v, J, a.c, 0, (int64_t)M * M, M);
   RHQR_LAUNCH_CHECK();
   RHQR_TRY(arnoldi_reflect<T>(a, w, h, info, st));
   if (qn != nullptr) RHQR_TRY(arnoldi_basis<T>(a, qn, st));
@@ -654,25 +708,23 @@ static rhqr_status arnoldi_step_t(ArnoldiState &a, const T *w, double *h, T *qn,
 // the newest column of U is stored unscaled (deferred scaling): scale it in a copy
 rhqr_status arnoldi_scale_copy(const ArnoldiState &a, void *Udst, int64_t ldu, cudaStream_t st) {
   if (a.j < 1) return RHQR_OK;
+  const dim3 g((unsigned)ceil_div(a.n, 256), (unsigned)a.nrhs);
   if (a.dtype == RHQR_F64)
-    left_scale_last_kernel<double><<<(unsigned)ceil_div(a.n, 256), 256, 0, st>>>((double *)Udst, ldu, a.n, a.j - 1,
-                                                                                 a.gamma, a.scaling == 0);
+    left_scale_last_kernel<double><<<g, 256, 0, st>>>((double *)Udst, ldu, a.n, a.j - 1, a.gamma, a.scaling == 0,
+                                                      ldu * a.M, a.M);
   else
-    left_scale_last_kernel<float><<<(unsigned)ceil_div(a.n, 256), 256, 0, st>>>((float *)Udst, ldu, a.n, a.j - 1,
-                                                                                a.gamma, a.scaling == 0);
+    left_scale_last_kernel<float><<<g, 256, 0, st>>>((float *)Udst, ldu, a.n, a.j - 1, a.gamma, a.scaling == 0,
+                                                     ldu * a.M, a.M);
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }
 
-rhqr_status arnoldi_begin(ArnoldiState &a, const void *r0, double *h0, void *q1, rhqr_info *info,
-                          cudaStream_t st) {
-  if (a.dtype == RHQR_F64)
-    return arnoldi_begin_t<double>(a, (const double *)r0, h0, (double *)q1, info, st);
+rhqr_status arnoldi_begin(ArnoldiState &a, const void *r0, double *h0, void *q1, rhqr_info *info, cudaStream_t st) {
+  if (a.dtype == RHQR_F64) return arnoldi_begin_t<double>(a, (const double *)r0, h0, (double *)q1, info, st);
   return arnoldi_begin_t<float>(a, (const float *)r0, h0, (float *)q1, info, st);
 }
 
 rhqr_status arnoldi_step(ArnoldiState &a, const void *w, double *h, void *qn, rhqr_info *info, cudaStream_t st) {
-  if (a.j < 1 || a.j >= a.M) return RHQR_EINVAL;
   if (a.dtype == RHQR_F64) return arnoldi_step_t<double>(a, (const double *)w, h, (double *)qn, info, st);
   return arnoldi_step_t<float>(a, (const float *)w, h, (float *)qn, info, st);
 }
@@ -685,10 +737,19 @@ rhqr_status arnoldi_step(ArnoldiState &a, const void *w, double *h, void *qn, rh
 // by Givens rotations in float64: thread 0 rotates column after column (the
 // column being rotated and the rotations live in shared memory, the triangle
 // R goes to `Rs`, ld = m), then the warp back-substitutes by columns (lane i
-// keeps the partial sum of row i).  res = || h0 - H y ||.
+// keeps the partial sum of row i).  res = || h0 - H y ||.  One warp per
+// process (blockIdx.x): H at H + b bs_H, h0 at h0 + b M, y at y + b bs_y.
 __global__ void arnoldi_lsq_kernel(const double *H, int64_t ldh, int32_t m, int32_t M, const double *h0, double *Rs,
-                                   double *y, double *res) {
+                                   double *y, double *res, int64_t bs_H, int64_t bs_y) {
   extern __shared__ double sh[];
+  {
+    const int64_t b = blockIdx.x;
+    H += b * bs_H;
+    h0 += b * M;
+    Rs += b * (int64_t)M * M;
+    y += b * bs_y;
+    res += b;
+  }
   double *col = sh;          // [m + 1]
   double *cs = sh + m + 1;   // [m]
   double *sn = cs + m;       // [m]
@@ -748,9 +809,17 @@ __global__ void arnoldi_lsq_kernel(const double *H, int64_t ldh, int32_t m, int3
 
 // coef = T_m (S_m^t y) with S_m = rows 0..m-1 of S's first m columns (the
 // identity top block of Psi keeps [y; 0] unchanged): v_i = sum_{j >= i} S_ji y_j,
-// coef_l = sum_{i >= l} T_li v_i
+// coef_l = sum_{i >= l} T_li v_i.  One block per process.
 __global__ void arnoldi_solution_coef_kernel(const double *T, int32_t M, const double *S, int64_t lds, int32_t m,
-                                             const double *y, double *v, double *coef) {
+                                             const double *y, double *v, double *coef, int64_t bs_S, int64_t bs_y) {
+  {
+    const int64_t b = blockIdx.x;
+    T += b * (int64_t)M * M;
+    S += b * bs_S;
+    y += b * bs_y;
+    v += b * M;
+    coef += b * M;
+  }
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     double acc = 0.0;
     for (int j = i; j < m; ++j) acc += S[(int64_t)i * lds + j] * y[j];
@@ -764,10 +833,19 @@ __global__ void arnoldi_solution_coef_kernel(const double *T, int32_t M, const d
   }
 }
 
-// x = x0 + [y; 0] - U_m coef (columns 0..m-1 of U are scaled once m steps were taken)
-template <class T>
+// x = x0 + [y; 0] - U_m coef (columns 0..m-1 of U are scaled once m steps were
+// taken); process blockIdx.y, its x0 and x at + b n.
+template <class T, class TX>
 __global__ void arnoldi_x_kernel(const T *U, int64_t ldu, int64_t n, int32_t m, const double *coef,
-                                 const double *y, const T *x0, T *x) {
+                                 const double *y, const TX *x0, TX *x, int64_t bs_U, int32_t M, int64_t bs_y) {
+  {
+    const int64_t b = blockIdx.y;
+    U += b * bs_U;
+    coef += b * M;
+    y += b * bs_y;
+    x0 += b * n;
+    x += b * n;
+  }
   __shared__ double c_s[1024];
   for (int l = threadIdx.x; l < m; l += blockDim.x) c_s[l] = coef[l];
   __syncthreads();
@@ -775,28 +853,40 @@ __global__ void arnoldi_x_kernel(const T *U, int64_t ldu, int64_t n, int32_t m, 
   if (i >= n) return;
   double acc = (double)x0[i] + (i < m ? y[i] : 0.0);
   for (int l = 0; l < m; ++l) acc -= (double)U[(int64_t)l * ldu + i] * c_s[l];
-  x[i] = (T)acc;
+  x[i] = (TX)acc;
 }
 
-size_t arnoldi_solution_scratch_doubles(int32_t M) { return (size_t)M * M + 2 * (size_t)M; }
+size_t arnoldi_solution_scratch_doubles(int32_t M, int32_t nrhs) {
+  return ((size_t)M * M + 2 * (size_t)M) * (size_t)nrhs;
+}
 
 rhqr_status arnoldi_solution(const ArnoldiState &a, double *scratch, const double *H, int64_t ldh, int32_t m,
-                             const double *h0, const void *x0, void *x, double *y, double *res, cudaStream_t st) {
+                             const double *h0, const void *x0, void *x, int32_t xdt, double *y, double *res,
+                             cudaStream_t st) {
   if (m < 1 || m > a.j - 1 || m > a.M - 1 || ldh < m + 1) return RHQR_EINVAL;
-  double *Rs = scratch, *v = scratch + (size_t)a.M * a.M, *coef = v + a.M;
+  if (xdt != RHQR_F64 && xdt != RHQR_F32) return RHQR_EINVAL;
+  const int32_t B = a.nrhs, M = a.M;
+  double *Rs = scratch, *v = scratch + (size_t)M * M * B, *coef = v + (size_t)M * B;
+  const int64_t bs_H = ldh * (M - 1), bs_y = M - 1;  // per process: H is (mmax+1) x mmax, y has mmax entries
   const size_t smem = sizeof(double) * (4 * (size_t)m + 2);  // column, cosines, sines, rotated h0
-  arnoldi_lsq_kernel<<<1, 32, smem, st>>>(H, ldh, m, a.M, h0, Rs, y, res);
+  arnoldi_lsq_kernel<<<(unsigned)B, 32, smem, st>>>(H, ldh, m, M, h0, Rs, y, res, bs_H, bs_y);
   RHQR_LAUNCH_CHECK();
   if (x == nullptr) return RHQR_OK;
-  arnoldi_solution_coef_kernel<<<1, 256, 0, st>>>(a.T, a.M, a.S, a.lds, m, y, v, coef);
+  arnoldi_solution_coef_kernel<<<(unsigned)B, 256, 0, st>>>(a.T, M, a.S, a.lds, m, y, v, coef, a.lds * M, bs_y);
   RHQR_LAUNCH_CHECK();
-  const unsigned grid = (unsigned)ceil_div(a.n, (int64_t)256);
-  if (a.dtype == RHQR_F64)
-    arnoldi_x_kernel<double><<<grid, 256, 0, st>>>((const double *)a.U, a.ldu, a.n, m, coef, y, (const double *)x0,
-                                                   (double *)x);
+  const dim3 grid((unsigned)ceil_div(a.n, (int64_t)256), (unsigned)B);
+  if (a.dtype == RHQR_F64 && xdt == RHQR_F64)
+    arnoldi_x_kernel<double, double><<<grid, 256, 0, st>>>((const double *)a.U, a.ldu, a.n, m, coef, y,
+                                                           (const double *)x0, (double *)x, a.ldu * M, M, bs_y);
+  else if (a.dtype == RHQR_F64)
+    arnoldi_x_kernel<double, float><<<grid, 256, 0, st>>>((const double *)a.U, a.ldu, a.n, m, coef, y,
+                                                          (const float *)x0, (float *)x, a.ldu * M, M, bs_y);
+  else if (xdt == RHQR_F64)
+    arnoldi_x_kernel<float, double><<<grid, 256, 0, st>>>((const float *)a.U, a.ldu, a.n, m, coef, y,
+                                                          (const double *)x0, (double *)x, a.ldu * M, M, bs_y);
   else
-    arnoldi_x_kernel<float><<<grid, 256, 0, st>>>((const float *)a.U, a.ldu, a.n, m, coef, y, (const float *)x0,
-                                                  (float *)x);
+    arnoldi_x_kernel<float, float><<<grid, 256, 0, st>>>((const float *)a.U, a.ldu, a.n, m, coef, y,
+                                                         (const float *)x0, (float *)x, a.ldu * M, M, bs_y);
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }

@@ -11,14 +11,15 @@ import torch
 
 from . import (ALG_LEFT, ALG_REC, BF16, F16, F32, F64, GAUSSIAN, SRHT, colmajor, dtype_code, ld_of, read_info,
                rhqr_batch_create, rhqr_batch_destroy, rhqr_batch_get_tuning, rhqr_batch_set_tuning, rhqr_batch_tune,
-               rhqr_batch_workspace_size, rhqr_factor_batched, rhqr_arnoldi_begin, rhqr_arnoldi_create, rhqr_arnoldi_destroy, rhqr_arnoldi_export, rhqr_arnoldi_step,
+               rhqr_batch_workspace_size, rhqr_factor_batched, rhqr_arnoldi_begin, rhqr_arnoldi_create_batch,
+               rhqr_stencil_apply, rhqr_stencil_residual, rhqr_stencil_residual_workspace, rhqr_arnoldi_solution_x, rhqr_arnoldi_destroy, rhqr_arnoldi_export, rhqr_arnoldi_step,
                rhqr_default_opts, rhqr_factor, rhqr_pipeline_create, rhqr_pipeline_destroy, rhqr_pipeline_submit,
                rhqr_pipeline_wait, rhqr_arnoldi_solution, rhqr_blas2_rgs, rhqr_blas2_rgs_workspace, rhqr_reconstruct,
                rhqr_trim_factor, rhqr_trim_workspace, rhqr_sketch_apply, rhqr_sketch_apply_workspace,
                rhqr_sketch_create, rhqr_sketch_destroy, rhqr_sketch_export, rhqr_sketch_shape, rhqr_workspace_size)
 
 TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}
-__all__ = ["Sketch", "Arnoldi", "GMRES", "Batch", "Pipeline", "factor", "trim_factor", "reconstruct", "colmajor", "ALG_LEFT", "ALG_REC", "GAUSSIAN", "SRHT"]
+__all__ = ["Sketch", "Arnoldi", "GMRES", "StencilOperator", "block", "Batch", "Pipeline", "factor", "trim_factor", "reconstruct", "colmajor", "ALG_LEFT", "ALG_REC", "GAUSSIAN", "SRHT"]
 
 
 class Sketch:
@@ -198,13 +199,18 @@ def info(out) -> dict:
 
 
 class Arnoldi:
-    """Owner of an rhqr_arnoldi handle (Algorithm 7 with a caller-applied operator)."""
+    """Owner of an rhqr_arnoldi handle (Algorithm 7 with a caller-applied
+    operator) over nrhs processes at once.  Vectors are tensors of shape (n,)
+    for one process or column-major (n, nrhs) blocks (see :func:`block`);
+    the Hessenberg columns come back as (M,) or (M, nrhs)."""
 
-    def __init__(self, sk: Sketch, n: int, mmax: int, dtype=torch.float64, scaling: int = 0, device="cuda"):
-        self.n, self.mmax, self.M, self.dtype, self.device = n, mmax, mmax + 1, dtype, device
+    def __init__(self, sk: Sketch, n: int, mmax: int, dtype=torch.float64, scaling: int = 0, device="cuda",
+                 nrhs: int = 1):
+        self.n, self.mmax, self.M, self.dtype, self.device, self.nrhs = n, mmax, mmax + 1, dtype, device, nrhs
         self.k = sk.k
-        self.handle = rhqr_arnoldi_create(sk.handle, n, mmax, dtype_code(torch.empty(0, dtype=dtype)), scaling)
-        self.info = torch.zeros(4, dtype=torch.int32, device=device)
+        self.handle = rhqr_arnoldi_create_batch(sk.handle, n, mmax, nrhs, dtype_code(torch.empty(0, dtype=dtype)),
+                                                scaling)
+        self.info = torch.zeros((nrhs, 4), dtype=torch.int32, device=device)
 
     def close(self):
         if self.handle:
@@ -217,76 +223,152 @@ class Arnoldi:
         except Exception:
             pass
 
+    def _vec(self, rows, dtype):
+        if self.nrhs == 1:
+            return torch.zeros(rows, dtype=dtype, device=self.device)
+        return block(rows, self.nrhs, dtype, self.device)
+
     def begin(self, r0: torch.Tensor):
-        h0 = torch.zeros(self.M, dtype=torch.float64, device=self.device)
-        q = torch.zeros(self.n, dtype=self.dtype, device=self.device)
+        h0 = self._vec(self.M, torch.float64)
+        q = self._vec(self.n, self.dtype)
         rhqr_arnoldi_begin(self.handle, r0, h0, q, self.info)
         return h0, q
 
     def step(self, w: torch.Tensor):
-        h = torch.zeros(self.M, dtype=torch.float64, device=self.device)
-        q = torch.zeros(self.n, dtype=self.dtype, device=self.device)
+        h = self._vec(self.M, torch.float64)
+        q = self._vec(self.n, self.dtype)
         rhqr_arnoldi_step(self.handle, w, h, q, self.info)
         return h, q
 
     def solution(self, H: torch.Tensor, m: int, h0: torch.Tensor, x0=None, x=None):
         """rhqr_arnoldi_solution: y = argmin ||h0 - H[:m+1, :m] y|| and, when x0
-        is given, x = x0 + Q_m y (into x, default a new tensor).  H is the
-        column-major (mmax+1) x mmax float64 matrix of the step outputs."""
-        y = torch.zeros(max(m, 1), dtype=torch.float64, device=self.device)
-        res = torch.zeros(1, dtype=torch.float64, device=self.device)
+        is given, x = x0 + Q_m y (into x, default a new tensor).  For one
+        process H is the column-major (mmax+1) x mmax float64 matrix of the
+        step outputs; for a batch, a (nrhs, mmax, mmax+1) tensor whose slice b
+        holds process b's matrix column by column (see :meth:`hessenberg`)."""
+        ldh = ld_of(H) if H.dim() == 2 else H.shape[2]
+        y = self._vec(max(self.mmax, 1), torch.float64)
+        res = torch.zeros(self.nrhs, dtype=torch.float64, device=self.device)
         if x0 is not None and x is None:
             x = torch.empty_like(x0)
-        rhqr_arnoldi_solution(self.handle, H, ld_of(H), m, h0, x0, x, y, res)
-        return y[:m], res, x
+        xdt = dtype_code(x0) if x0 is not None else dtype_code(torch.empty(0, dtype=self.dtype))
+        rhqr_arnoldi_solution_x(self.handle, H, ldh, m, h0, x0, x, xdt, y, res)
+        return y[:m], (res if self.nrhs > 1 else res[:1]), x
+
+    def hessenberg(self):
+        """Storage for the Hessenberg columns of all processes."""
+        if self.nrhs == 1:
+            return colmajor(torch.zeros((self.M, self.mmax), dtype=torch.float64, device=self.device))
+        return torch.zeros((self.nrhs, self.mmax, self.M), dtype=torch.float64, device=self.device)
 
     def export(self):
-        U = colmajor(torch.zeros((self.n, self.M), dtype=self.dtype, device=self.device))
-        S = colmajor(torch.zeros((self.k + self.M, self.M), dtype=torch.float64, device=self.device))
-        T = torch.zeros((self.M, self.M), dtype=torch.float64, device=self.device)
+        """U, S, T of every process (process b: U[:, b M:(b+1) M] ...); for one
+        process as before."""
+        B = self.nrhs
+        U = colmajor(torch.zeros((self.n, self.M * B), dtype=self.dtype, device=self.device))
+        S = colmajor(torch.zeros((self.k + self.M, self.M * B), dtype=torch.float64, device=self.device))
+        T = torch.zeros((B, self.M, self.M), dtype=torch.float64, device=self.device)
         cnt = rhqr_arnoldi_export(self.handle, U, ld_of(U), S, ld_of(S), T)
-        return U, S, T.t(), cnt
+        Tt = T.transpose(1, 2)
+        return U, S, (Tt[0] if B == 1 else Tt), cnt
+
+
+def block(rows: int, cols: int, dtype, device="cuda") -> torch.Tensor:
+    """A zero column-major (rows, cols) tensor with leading dimension rows."""
+    return torch.zeros((cols, rows), dtype=dtype, device=device).t()
+
+
+class StencilOperator:
+    """The library's matrix-free convection-diffusion operator on a g x g grid
+    (rhqr_stencil_apply) and its restart residual (rhqr_stencil_residual)."""
+
+    def __init__(self, g: int, peclet: float = 10.0, nrhs: int = 1, device="cuda"):
+        self.g, self.pe, self.nrhs, self.n = g, peclet, nrhs, g * g
+        self.wbytes = rhqr_stencil_residual_workspace(g, nrhs)
+        self.work = torch.empty(max(self.wbytes, 1), dtype=torch.uint8, device=device)
+        self.norms = torch.zeros(2 * nrhs, dtype=torch.float64, device=device)
+
+    def __call__(self, X: torch.Tensor) -> torch.Tensor:
+        Y = torch.empty_like(X) if X.dim() == 1 else block(self.n, X.shape[1], X.dtype, X.device)
+        rhqr_stencil_apply(self.g, self.pe, X, dtype_code(X), 1 if X.dim() == 1 else X.shape[1], Y)
+        return Y
+
+    def residual(self, B: torch.Tensor, X: torch.Tensor, rdtype=None):
+        """R = B - A X (formed in float64, returned in rdtype, default B's) and
+        the device tensors ||B[:, b] - A X[:, b]||, ||B[:, b]||."""
+        nr = 1 if B.dim() == 1 else B.shape[1]
+        rdtype = rdtype or B.dtype
+        R = torch.empty(B.shape, dtype=rdtype, device=B.device) if B.dim() == 1 else block(self.n, nr, rdtype, B.device)
+        rhqr_stencil_residual(self.g, self.pe, B, X, dtype_code(B), nr, R, dtype_code(R), self.norms, self.work,
+                              self.wbytes)
+        return R, self.norms[0:2 * nr:2], self.norms[1:2 * nr:2]
 
 
 class GMRES:
-    """Restarted RHQR-GMRES (Algorithm 8) over the library's Arnoldi steps with a
-    caller-applied operator A (a function of a device vector).  Each cycle takes
-    up to `restart` steps from r0 = b - A x, checks the sketched residual
-    ||h0 - H y|| (= ||Psi (b - A x)||) every `check` steps, and updates x by
-    rhqr_arnoldi_solution; it stops when the true residual ||b - A x|| <= tol ||b||."""
+    """Restarted RHQR-GMRES (Algorithm 8) for nrhs right-hand sides at once,
+    over the library's batched Arnoldi steps with a caller-applied operator A
+    (a function of an (n,) vector or an (n, nrhs) column-major block).  Each
+    cycle starts from R = B - A X (the library's residual kernel when A has a
+    `residual` method, as StencilOperator does), takes up to `restart` steps,
+    checks the sketched residuals ||h0 - H y|| (= ||Psi (b - A x)||) every
+    `check` steps and updates every X by rhqr_arnoldi_solution; it stops when
+    ||b - A x|| <= tol ||b|| for every right-hand side.  B and X may be wider
+    than the basis dtype (float64 with a float32 basis): the residual is then
+    formed in float64 and every cycle's float32 correction is added to the
+    float64 iterate by the library (rhqr_arnoldi_solution_x)."""
 
-    def __init__(self, sk: Sketch, n: int, restart: int, dtype=torch.float64, device="cuda"):
-        self.arn = Arnoldi(sk, n, restart, dtype=dtype, device=device)
-        self.restart, self.n, self.dtype, self.device = restart, n, dtype, device
-        self.H = colmajor(torch.zeros((restart + 1, restart), dtype=torch.float64, device=device))
+    def __init__(self, sk: Sketch, n: int, restart: int, dtype=torch.float64, device="cuda", nrhs: int = 1):
+        self.arn = Arnoldi(sk, n, restart, dtype=dtype, device=device, nrhs=nrhs)
+        self.restart, self.n, self.dtype, self.device, self.nrhs = restart, n, dtype, device, nrhs
+        self.H = self.arn.hessenberg()
 
     def close(self):
         self.arn.close()
 
-    def solve(self, A, b: torch.Tensor, x0=None, tol: float = 1e-8, max_cycles: int = 50, check: int = 10):
-        x = torch.zeros_like(b) if x0 is None else x0.clone()
-        bnorm = float(torch.linalg.norm(b.double()))
+    def _residual(self, A, B, X):
+        """R = B - A X in the basis dtype, with the norms of the residual and of B."""
+        if hasattr(A, "residual"):
+            R, rn, bn = A.residual(B, X, rdtype=self.dtype)
+            return R, rn.cpu().numpy(), bn.cpu().numpy()
+        # a caller-supplied operator: its residual is the caller's arithmetic
+        R = B - A(X)
+        Rd, Bd = R.double(), B.double()
+        if R.dim() == 1:
+            return (R.to(self.dtype), torch.linalg.norm(Rd).reshape(1).cpu().numpy(),
+                    torch.linalg.norm(Bd).reshape(1).cpu().numpy())
+        return (R.to(self.dtype), torch.linalg.norm(Rd, dim=0).cpu().numpy(),
+                torch.linalg.norm(Bd, dim=0).cpu().numpy())
+
+    def solve(self, A, B: torch.Tensor, x0=None, tol: float = 1e-8, max_cycles: int = 50, check: int = 10):
+        """Returns X and the history of max_b ||b - A x|| / ||b|| per cycle."""
+        if x0 is not None:
+            X = x0.clone() if B.dim() == 1 else block(self.n, B.shape[1], B.dtype, B.device).copy_(x0)
+        else:
+            X = torch.zeros_like(B) if B.dim() == 1 else block(self.n, B.shape[1], B.dtype, B.device)
         history = []
         for cycle in range(max_cycles):
-            r = b - A(x)
-            rnorm = float(torch.linalg.norm(r.double()))
-            history.append(rnorm / bnorm)
-            if rnorm <= tol * bnorm:
-                return x, history
-            h0, q = self.arn.begin(r)
+            R, rn, bn = self._residual(A, B, X)
+            rel = rn / bn
+            history.append(float(rel.max()))
+            if (rn <= tol * bn).all():
+                return X, history
+            h0, q = self.arn.begin(R)
             steps = 0
             for j in range(self.restart):
                 h, q = self.arn.step(A(q))
-                self.H[:, j] = h
+                if self.nrhs == 1:
+                    self.H[:, j] = h
+                else:
+                    self.H[:, j, :] = h.t()
                 steps = j + 1
                 if steps % check == 0 and steps < self.restart:
                     _, res, _ = self.arn.solution(self.H, steps, h0)
-                    if float(res) <= 0.5 * tol * bnorm:
+                    if (res.cpu().numpy() <= 0.5 * tol * bn).all():
                         break
-            _, _, x = self.arn.solution(self.H, steps, h0, x0=x, x=x)
-        r = b - A(x)
-        history.append(float(torch.linalg.norm(r.double())) / bnorm)
-        return x, history
+            _, _, X = self.arn.solution(self.H, steps, h0, x0=X, x=X)
+        _, rn, bn = self._residual(A, B, X)
+        history.append(float((rn / bn).max()))
+        return X, history
 
 
 class Batch:

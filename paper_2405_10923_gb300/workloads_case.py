@@ -154,43 +154,51 @@ def main():
         n, mmax, k = g * g, 100, 400
         sk = ta.Sketch(n, k, rh.SRHT, 2005)
         for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
-            b = torch.tensor(np.random.default_rng(1005).standard_normal(n), dtype=dt, device="cuda")
-            arn = ta.Arnoldi(sk, n, mmax, dtype=dt)
+            for nrhs in (1, 32):
+                op = ta.StencilOperator(g, nrhs=nrhs)
+                rng = np.random.default_rng(1005)
+                if nrhs == 1:
+                    b = torch.tensor(rng.standard_normal(n), dtype=dt, device="cuda")
+                else:
+                    b = ta.block(n, nrhs, dt).copy_(torch.tensor(rng.standard_normal((n, nrhs)), dtype=dt))
+                arn = ta.Arnoldi(sk, n, mmax, dtype=dt, nrhs=nrhs)
 
-            def cycle():
-                _, q = arn.begin(b)
-                for _ in range(mmax):
-                    _, q = arn.step(ri.stencil_apply(q, g))
-                return q
+                def cycle():
+                    _, q = arn.begin(b)
+                    for _ in range(mmax):
+                        _, q = arn.step(op(q))
+                    return q
 
-            # rebuild the handle each cycle (begin restarts it)
-            ms = _time(cycle, a.reps)
-            U, S, T, cnt = arn.export()
-            emit(case="arnoldi", path=f"RHQR-Arnoldi {name} basis", n=n, steps=mmax, k=k, sketch="srht",
-                 ms_per_cycle=ms, us_per_step=ms * 1e3 / mmax, reflectors=cnt,
-                 basis_gb=n * (mmax + 1) * b.element_size() / 1e9)
-            arn.close()
+                ms = _time(cycle, a.reps)
+                emit(case="arnoldi", path=f"RHQR-Arnoldi {name} basis, {nrhs} right-hand side(s) per launch", n=n,
+                     steps=mmax, k=k, nrhs=nrhs, sketch="srht", ms_per_cycle=ms, us_per_step=ms * 1e3 / mmax,
+                     us_per_step_per_rhs=ms * 1e3 / mmax / nrhs,
+                     basis_gb=n * (mmax + 1) * b.element_size() * nrhs / 1e9)
+                arn.close()
         sk.close()
     if "gmres" in a.cases:
         g = 1024
-        n, restart, k = g * g, 100, 400
+        n, restart, k, nrhs = g * g, 100, 400, 32
         sk = ta.Sketch(n, k, rh.SRHT, 2005)
-        b = torch.tensor(np.random.default_rng(1005).standard_normal(n), dtype=torch.float64, device="cuda")
-        solver = ta.GMRES(sk, n, restart)
-        A = lambda v: ri.stencil_apply(v.clone(), g)  # noqa: E731
-        solver.solve(A, b, tol=1e-8, max_cycles=1)  # warm-up
-        torch.cuda.synchronize()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record()
-        x, hist = solver.solve(A, b, tol=1e-8, max_cycles=a.cycles)
-        t1.record()
-        torch.cuda.synchronize()
-        cycles = len(hist) - 1
-        emit(case="gmres", path="restarted RHQR-GMRES f64", n=n, restart=restart, k=k, sketch="srht",
-             cycles=cycles, ms_per_cycle=t0.elapsed_time(t1) / max(cycles, 1),
-             relative_residuals=[float(f"{h:.3e}") for h in hist])
-        solver.close()
+        op = ta.StencilOperator(g, nrhs=nrhs)
+        B = ta.block(n, nrhs, torch.float64).copy_(
+            torch.tensor(np.random.default_rng(1005).standard_normal((n, nrhs))))
+        for dt, name in ((torch.float32, "f32 basis, f64 iterate"), (torch.float64, "f64 basis")):
+            solver = ta.GMRES(sk, n, restart, dtype=dt, nrhs=nrhs)
+            solver.solve(op, B, tol=1e-8, max_cycles=1)  # warm-up
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record()
+            X, hist = solver.solve(op, B, tol=1e-8, max_cycles=a.cycles)
+            t1.record()
+            torch.cuda.synchronize()
+            cycles = len(hist) - 1
+            emit(case="gmres", path=f"restarted RHQR-GMRES, {name}", n=n, restart=restart, k=k, nrhs=nrhs,
+                 sketch="srht", cycles=cycles, converged=bool(hist[-1] <= 1e-8), total_s=t0.elapsed_time(t1) / 1e3,
+                 ms_per_cycle=t0.elapsed_time(t1) / max(cycles, 1),
+                 max_relative_residuals=[float(f"{h:.3e}") for h in hist])
+            solver.close()
         sk.close()
 
 
