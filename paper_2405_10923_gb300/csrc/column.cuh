@@ -6,6 +6,8 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "fwht.cuh"
+#include "sketch.cuh"
 
 namespace rhqr {
 
@@ -149,6 +151,70 @@ __global__ void left_column_srht_kernel(ColArgs a0, const uint32_t *sign_bits, i
   }
   T *ys = Ystage + (int64_t)blockIdx.x * d2;
   for (int s = threadIdx.x; s < d2; s += blockDim.x) ys[s] = v[i2_list[s]];
+}
+
+// The refreshed column j (stored in U) of problem blockIdx.y: rows >= skm
+// signed, segment blockIdx.x transformed by fwht_segment (N2 = 2^LOGN2 >=
+// 512), the sampled in-segment positions kept.
+template <class T, int LOGN2>
+__global__ void __launch_bounds__(1 << (LOGN2 - 4)) column_srht_fwht_kernel(ColArgs a0, const uint32_t *sign_bits,
+                                                                            const int32_t *i2_list, int32_t d2,
+                                                                            T *Ystage) {
+  constexpr int N2 = 1 << LOGN2, NT = N2 / 16;
+  const ColArgs a = batch_args<T>(a0);
+  Ystage += (int64_t)blockIdx.y * a0.bt.stage;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *buf = reinterpret_cast<T *>(smem_raw);
+  const int t = threadIdx.x;
+  const int64_t row0 = (int64_t)blockIdx.x * N2;
+  const T *u = (const T *)a.U + (int64_t)a.j * a.ldu;
+  T v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int64_t i = row0 + r * NT + t;
+    T val = T(0);
+    if (i >= a.skm && i < a.n) {
+      val = u[i];
+      if ((sign_bits[i >> 5] >> (i & 31)) & 1u) val = -val;
+    }
+    v[r] = val;
+  }
+  fwht_segment<T, LOGN2>(v, buf);
+  T *ys = Ystage + (int64_t)blockIdx.x * d2;
+  for (int s = t; s < d2; s += NT) ys[s] = buf[i2_list[s]];
+}
+
+template <class T, int LOGN2>
+static rhqr_status launch_column_fwht(const ColArgs &ca, const SketchView &v, T *stage, unsigned nprob,
+                                      cudaStream_t st) {
+  const size_t smem = sizeof(T) << LOGN2;
+  if (smem > 48 * 1024)
+    RHQR_CUDA_TRY(cudaFuncSetAttribute(column_srht_fwht_kernel<T, LOGN2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+  column_srht_fwht_kernel<T, LOGN2><<<dim3((unsigned)v.N1, nprob), 1 << (LOGN2 - 4), smem, st>>>(
+      ca, v.sign_bits, v.i2_list, v.d2, stage);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
+}
+
+// Stage A of the SRHT of the refreshed column(s) (nprob problems of a batch):
+// the register / shuffle transform for segments of 512 entries or more, else
+// the shared-memory kernel.
+template <class T>
+static rhqr_status column_srht(const ColArgs &ca, const SketchView &v, T *stage, unsigned nprob, cudaStream_t st) {
+  switch (v.N2) {
+    case 8192: return launch_column_fwht<T, 13>(ca, v, stage, nprob, st);
+    case 4096: return launch_column_fwht<T, 12>(ca, v, stage, nprob, st);
+    case 2048: return launch_column_fwht<T, 11>(ca, v, stage, nprob, st);
+    case 1024: return launch_column_fwht<T, 10>(ca, v, stage, nprob, st);
+    case 512: return launch_column_fwht<T, 9>(ca, v, stage, nprob, st);
+    default: break;
+  }
+  const size_t smem = (size_t)v.N2 * sizeof(T);
+  left_column_srht_kernel<T, true><<<dim3((unsigned)v.N1, nprob), 512, smem, st>>>(ca, v.sign_bits, v.N2, v.i2_list,
+                                                                                  v.d2, stage);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
 }
 
 template <class T>

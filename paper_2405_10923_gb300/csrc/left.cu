@@ -210,12 +210,7 @@ static rhqr_status left_typed(const SketchView &s, const T *W, int64_t n, int32_
       // refresh with the whole GPU, then sign / transform / sample the refreshed column
       left_refresh_kernel<T><<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8), 256, 0, st>>>(ca);
       RHQR_LAUNCH_CHECK();
-      size_t smem = (size_t)s.N2 * sizeof(T);
-      if (smem > 48 * 1024)
-        RHQR_CUDA_TRY(cudaFuncSetAttribute(left_column_srht_kernel<T, true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      left_column_srht_kernel<T, true><<<s.N1, 512, smem, st>>>(ca, s.sign_bits, s.N2, s.i2_list, s.d2, (T *)stage);
-      RHQR_LAUNCH_CHECK();
+      RHQR_TRY(column_srht<T>(ca, s, (T *)stage, 1, st));
       left_srht_combine_kernel<T><<<(unsigned)ceil_div(s.k, 128), 128, 0, st>>>(
           (const T *)stage, s.N1, s.d2, s.sample_i1, s.sample_slot, s.k, m, scale, y);
       RHQR_LAUNCH_CHECK();
@@ -427,12 +422,7 @@ static rhqr_status block_typed(const SketchView &s, const T *W, int64_t n, int32
       if (s.kind == RHQR_SKETCH_SRHT) {
         left_refresh_kernel<T><<<upd_grid, 256, 0, st>>>(ca);
         RHQR_LAUNCH_CHECK();
-        size_t smem = (size_t)s.N2 * sizeof(T);
-        if (smem > 48 * 1024)
-          RHQR_CUDA_TRY(cudaFuncSetAttribute(left_column_srht_kernel<T, true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        left_column_srht_kernel<T, true><<<s.N1, 512, smem, st>>>(ca, s.sign_bits, s.N2, s.i2_list, s.d2, (T *)stage);
-        RHQR_LAUNCH_CHECK();
+        RHQR_TRY(column_srht<T>(ca, s, (T *)stage, 1, st));
         left_srht_combine_kernel<T><<<(unsigned)ceil_div(s.k, 128), 128, 0, st>>>(
             (const T *)stage, s.N1, s.d2, s.sample_i1, s.sample_slot, s.k, m, scale, y);
         RHQR_LAUNCH_CHECK();
@@ -619,13 +609,7 @@ static rhqr_status arnoldi_reflect(ArnoldiState &a, const T *w, double *h, rhqr_
     dim3 gr((unsigned)std::min<int64_t>(ceil_div(a.n, 256), std::max<int64_t>(1, 152 * 8 / B)), (unsigned)B);
     left_refresh_kernel<T><<<gr, 256, 0, st>>>(ca);
     RHQR_LAUNCH_CHECK();
-    size_t smem = (size_t)a.view.N2 * sizeof(T);
-    if (smem > 48 * 1024)
-      RHQR_CUDA_TRY(cudaFuncSetAttribute(left_column_srht_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-    left_column_srht_kernel<T, true><<<dim3((unsigned)a.view.N1, (unsigned)B), 512, smem, st>>>(
-        ca, a.view.sign_bits, a.view.N2, a.view.i2_list, a.view.d2, (T *)a.stage);
-    RHQR_LAUNCH_CHECK();
+    RHQR_TRY(column_srht<T>(ca, a.view, (T *)a.stage, (unsigned)B, st));
     left_srht_combine_kernel<T><<<dim3((unsigned)ceil_div(a.view.k, 128), (unsigned)B), 128, 0, st>>>(
         (const T *)a.stage, a.view.N1, a.view.d2, a.view.sample_i1, a.view.sample_slot, a.view.k, M, scale, a.y,
         a.stage_elems, p);

@@ -13,6 +13,7 @@
 // float64 (or float32 within a K-chunk) accumulation and a fixed-order float64
 // reduction of the chunk partials.
 #include "common.cuh"
+#include "fwht.cuh"
 #include "sketch.cuh"
 
 namespace rhqr {
@@ -62,6 +63,50 @@ __global__ void srht_stage_a_kernel(const T *X, int64_t ldx, int64_t n, int32_t 
   }
   T *y = Y + ((int64_t)col * N1 + j1) * d2;
   for (int s = threadIdx.x; s < d2; s += blockDim.x) y[s] = v[i2_list[s]];
+}
+
+// SRHT stage A for segments of 512 .. 8192 entries: N2 / 16 threads, the
+// column's entries loaded straight into registers (coalesced, signs and the
+// zero rows applied on the way), transformed by fwht_segment, the sampled
+// in-block positions written out.
+template <class T, int LOGN2>
+__global__ void __launch_bounds__(1 << (LOGN2 - 4)) srht_stage_a_fwht_kernel(const T *X, int64_t ldx, int64_t n,
+                                                                             int32_t m, const uint32_t *sign_bits,
+                                                                             int32_t N1, const int32_t *i2_list,
+                                                                             int32_t d2, T *Y) {
+  constexpr int N2 = 1 << LOGN2, NT = N2 / 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *buf = reinterpret_cast<T *>(smem_raw);
+  const int j1 = blockIdx.x, col = blockIdx.y, t = threadIdx.x;
+  const T *x = X + (int64_t)col * ldx;
+  const int64_t row0 = (int64_t)j1 * N2;
+  T v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int64_t i = row0 + r * NT + t;
+    T val = T(0);
+    if (i >= m && i < n) {
+      val = x[i];
+      if ((sign_bits[i >> 5] >> (i & 31)) & 1u) val = -val;
+    }
+    v[r] = val;
+  }
+  fwht_segment<T, LOGN2>(v, buf);
+  T *y = Y + ((int64_t)col * N1 + j1) * d2;
+  for (int s = t; s < d2; s += NT) y[s] = buf[i2_list[s]];
+}
+
+template <class T, int LOGN2>
+static rhqr_status launch_stage_a_fwht(dim3 grid, const T *X, int64_t ldx, int64_t n, int32_t m,
+                                       const SketchView &s, T *Y, cudaStream_t st) {
+  const size_t smem = sizeof(T) << LOGN2;
+  if (smem > 48 * 1024)
+    RHQR_CUDA_TRY(cudaFuncSetAttribute(srht_stage_a_fwht_kernel<T, LOGN2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  srht_stage_a_fwht_kernel<T, LOGN2><<<grid, 1 << (LOGN2 - 4), smem, st>>>(X, ldx, n, m, s.sign_bits, s.N1,
+                                                                            s.i2_list, s.d2, Y);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
 }
 
 // SRHT stage B: Z[m + r, col] = (1/sqrt k) sum_{j1} (-1)^popc(i1_r & j1) Y[col, j1, slot_r]
@@ -191,12 +236,19 @@ static rhqr_status apply_typed(const SketchView &s, int32_t m, const TX *X, int6
     TX *Y = (TX *)ws;
     size_t need = (size_t)c * s.N1 * s.d2 * sizeof(TX);
     if (ws_bytes < need) return RHQR_ENOMEM;
-    size_t smem = (size_t)s.N2 * sizeof(TX);
-    if (smem > 48 * 1024) RHQR_CUDA_TRY(cudaFuncSetAttribute(srht_stage_a_kernel<TX>,
-                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 ga(s.N1, c);
-    srht_stage_a_kernel<TX><<<ga, 512, smem, st>>>(X, ldx, n, m, s.sign_bits, s.N2, s.N1, s.i2_list, s.d2, Y);
-    RHQR_LAUNCH_CHECK();
+    switch (s.N2) {
+      case 8192: RHQR_TRY((launch_stage_a_fwht<TX, 13>(ga, X, ldx, n, m, s, Y, st))); break;
+      case 4096: RHQR_TRY((launch_stage_a_fwht<TX, 12>(ga, X, ldx, n, m, s, Y, st))); break;
+      case 2048: RHQR_TRY((launch_stage_a_fwht<TX, 11>(ga, X, ldx, n, m, s, Y, st))); break;
+      case 1024: RHQR_TRY((launch_stage_a_fwht<TX, 10>(ga, X, ldx, n, m, s, Y, st))); break;
+      case 512: RHQR_TRY((launch_stage_a_fwht<TX, 9>(ga, X, ldx, n, m, s, Y, st))); break;
+      default: {  // short transforms: one butterfly level per step in shared memory
+        size_t smem = (size_t)s.N2 * sizeof(TX);
+        srht_stage_a_kernel<TX><<<ga, 512, smem, st>>>(X, ldx, n, m, s.sign_bits, s.N2, s.N1, s.i2_list, s.d2, Y);
+        RHQR_LAUNCH_CHECK();
+      }
+    }
     dim3 gb((unsigned)ceil_div(s.k, 128), c);
     srht_stage_b_kernel<TX><<<gb, 128, 0, st>>>(Y, s.N1, s.d2, s.sample_i1, s.sample_slot, s.k, m,
                                                  1.0 / sqrt((double)s.k), Z, ldz);

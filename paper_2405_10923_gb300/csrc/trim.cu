@@ -344,12 +344,7 @@ static rhqr_status trim_typed(const SketchView &s, const T *W, int64_t n, int32_
     if (s.kind == RHQR_SKETCH_SRHT) {
       left_refresh_kernel<T><<<grid, 256, 0, st>>>(ca);
       RHQR_LAUNCH_CHECK();
-      size_t smem = (size_t)s.N2 * sizeof(T);
-      if (smem > 48 * 1024)
-        RHQR_CUDA_TRY(cudaFuncSetAttribute(left_column_srht_kernel<T, true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      left_column_srht_kernel<T, true><<<s.N1, 512, smem, st>>>(ca, s.sign_bits, s.N2, s.i2_list, s.d2, (T *)stage);
-      RHQR_LAUNCH_CHECK();
+      RHQR_TRY(column_srht<T>(ca, s, (T *)stage, 1, st));
       left_srht_combine_kernel<T><<<(unsigned)ceil_div(k, 128), 128, 0, st>>>(
           (const T *)stage, s.N1, s.d2, s.sample_i1, s.sample_slot, k, 0, scale, zw);
       RHQR_LAUNCH_CHECK();

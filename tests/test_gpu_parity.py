@@ -99,6 +99,34 @@ def test_sketch_apply_f64(gpu_lib, kind, n, m, c, k):
     sk.close()
 
 
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("n,m,c,k", [(200, 3, 2, 16), (300, 0, 3, 40), (700, 5, 2, 64), (2000, 7, 1, 64),
+                                     (3000, 2, 4, 128), (6000, 9, 2, 256), ((1 << 20) + 5, 16, 2, 512)])
+def test_srht_every_segment_length(gpu_lib, dt, n, m, c, k):
+    """The SRHT's transform runs per segment of N2 = min(N, 8192) entries: in
+    shared memory one level at a time below 512 entries, by the register /
+    warp-shuffle / one-transpose kernel from 512 to 8192.  Every length against
+    the oracle's Sylvester transform (float64 to 1e-13; float32 within the
+    float32 bound gamma_{log2 N + 5} of the SRHT lemma)."""
+    from paper_2405_10923_gb300 import torch_api as ta
+
+    X = ri.gaussian(n, c, 8)
+    if dt == "f32":
+        X = X.astype(np.float32).astype(np.float64)
+    sk, osk = ta.Sketch(n, k, gpu_lib.SRHT, 9), sketch.SRHTSketch(n, k, 9)
+    Z = _np(sk.apply(_dev(X, torch.float64 if dt == "f64" else torch.float32), m))
+    Zo = sketch.rh_sketch(X, m, osk)
+    assert np.array_equal(Z[:m], Zo[:m])
+    if dt == "f64":
+        assert np.max(np.abs(Z - Zo)) <= 1e-13 * np.abs(Zo).max()
+    else:
+        lg = int(np.ceil(np.log2(n)))
+        gamma = (lg + 5) * 2.0**-24 / (1 - (lg + 5) * 2.0**-24)
+        colnorm = np.linalg.norm(X[m:], axis=0)
+        assert (np.abs(Z[m:] - Zo[m:]).max(axis=0) <= gamma * np.sqrt(2.0**lg / k) * colnorm).all()
+    sk.close()
+
+
 @pytest.mark.parametrize("kind", ["srht", "gaussian"])
 def test_sketch_apply_f32(gpu_lib, kind):
     from paper_2405_10923_gb300 import torch_api as ta
