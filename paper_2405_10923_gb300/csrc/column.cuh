@@ -79,31 +79,37 @@ __device__ __forceinline__ T refresh_row(const ColArgs &a, int64_t i, const doub
 template <class T>
 __global__ void __launch_bounds__(256) left_refresh_kernel(ColArgs a0) {
   const ColArgs a = batch_args<T>(a0);
-  __shared__ double c_s[1024];
-  const int j = a.j, lo = a.lo;
-  for (int l = threadIdx.x; l < j - lo; l += blockDim.x) c_s[l] = a.c[l];
+  __shared__ T c_s[1024];  // coefficients, converted once
+  const int j = a.j, lo = a.lo, nc = j - lo;
+  for (int l = threadIdx.x; l < nc; l += blockDim.x) c_s[l] = (T)a.c[l];
   const T inv_g = (j - 1 >= lo) ? (T)(1.0 / a.gamma[j - 1]) : T(1);
   __syncthreads();
   const T *W = (const T *)a.W;
   T *U = (T *)a.U;
+  const int64_t ldu = a.ldu;
+  // the fully scaled columns lo .. j-2 with eight independent loads and
+  // partial sums in flight per thread; column j-1 (deferred scale) last
+  const int nfull = nc > 0 ? nc - 1 : 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-    T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
-    int l = lo;
-    for (; l + 4 < j; l += 4) {
-      p0 += U[(int64_t)l * a.ldu + i] * (T)c_s[l - lo];
-      p1 += U[(int64_t)(l + 1) * a.ldu + i] * (T)c_s[l + 1 - lo];
-      p2 += U[(int64_t)(l + 2) * a.ldu + i] * (T)c_s[l + 2 - lo];
-      p3 += U[(int64_t)(l + 3) * a.ldu + i] * (T)c_s[l + 3 - lo];
+    T p[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) p[q] = T(0);
+    const T *up = U + (int64_t)lo * ldu + i;
+    int l = 0;
+    for (; l + 8 <= nfull; l += 8) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) p[q] += up[q * ldu] * c_s[l + q];
+      up += 8 * ldu;
     }
-    for (; l + 1 < j; ++l) p0 += U[(int64_t)l * a.ldu + i] * (T)c_s[l - lo];
-    T w = W[(int64_t)j * a.ldw + i] - ((p0 + p1) + (p2 + p3));
+    for (; l < nfull; ++l, up += ldu) p[l & 7] += *up * c_s[l];
+    T w = W[(int64_t)j * a.ldw + i] - (((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7])));
     if (j - 1 >= lo) {
-      T *up = U + (int64_t)(j - 1) * a.ldu + i;
-      const T u = (i < j - 1) ? T(0) : ((i == j - 1 && a.unit) ? T(1) : *up * inv_g);
-      *up = u;
-      w -= u * (T)c_s[j - 1 - lo];
+      T *ul = U + (int64_t)(j - 1) * ldu + i;
+      const T u = (i < j - 1) ? T(0) : ((i == j - 1 && a.unit) ? T(1) : *ul * inv_g);
+      *ul = u;
+      w -= u * c_s[nc - 1];
     }
-    U[(int64_t)j * a.ldu + i] = w;
+    U[(int64_t)j * ldu + i] = w;
     if (i < a.m) a.y[i] = (double)w;
   }
 }
@@ -217,21 +223,27 @@ static rhqr_status column_srht(const ColArgs &ca, const SketchView &v, T *stage,
   return RHQR_OK;
 }
 
+// Stage B of the SRHT of one column per problem (blockIdx.y): sampled row r
+// = i1 N2 + i2 sums its N1 segment values with the signs (-1)^popc(i1 & j1).
+// One warp per sampled row: lane l adds j1 = l, l + 32, ... and the lane sums
+// meet in a fixed tree.
 template <class T>
 __global__ void left_srht_combine_kernel(const T *Ystage, int32_t N1, int32_t d2, const int32_t *sample_i1,
                                          const int32_t *sample_slot, int32_t k, int32_t m, double scale, double *y,
                                          int64_t bs_stage = 0, int64_t bs_y = 0) {
   Ystage += (int64_t)blockIdx.y * bs_stage;
   y += (int64_t)blockIdx.y * bs_y;
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= k) return;
-  int i1 = sample_i1[r], slot = sample_slot[r];
+  const int i1 = sample_i1[r], slot = sample_slot[r];
   double acc = 0.0;
-  for (int j1 = 0; j1 < N1; ++j1) {
-    double t = (double)Ystage[(int64_t)j1 * d2 + slot];
+  for (int j1 = lane; j1 < N1; j1 += 32) {
+    const double t = (double)Ystage[(int64_t)j1 * d2 + slot];
     acc += (__popc(i1 & j1) & 1) ? -t : t;
   }
-  y[m + r] = acc * scale;
+  acc = warp_sum(acc);
+  if (lane == 0) y[m + r] = acc * scale;
 }
 
 // Gaussian: block owns rows [b*RB, (b+1)*RB); partial[b][r] = sum_i G[r, i] w_i over rows i >= m

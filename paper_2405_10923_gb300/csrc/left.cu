@@ -211,7 +211,7 @@ static rhqr_status left_typed(const SketchView &s, const T *W, int64_t n, int32_
       left_refresh_kernel<T><<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8), 256, 0, st>>>(ca);
       RHQR_LAUNCH_CHECK();
       RHQR_TRY(column_srht<T>(ca, s, (T *)stage, 1, st));
-      left_srht_combine_kernel<T><<<(unsigned)ceil_div(s.k, 128), 128, 0, st>>>(
+      left_srht_combine_kernel<T><<<(unsigned)ceil_div(s.k, 8), 256, 0, st>>>(
           (const T *)stage, s.N1, s.d2, s.sample_i1, s.sample_slot, s.k, m, scale, y);
       RHQR_LAUNCH_CHECK();
     } else {
@@ -423,7 +423,7 @@ static rhqr_status block_typed(const SketchView &s, const T *W, int64_t n, int32
         left_refresh_kernel<T><<<upd_grid, 256, 0, st>>>(ca);
         RHQR_LAUNCH_CHECK();
         RHQR_TRY(column_srht<T>(ca, s, (T *)stage, 1, st));
-        left_srht_combine_kernel<T><<<(unsigned)ceil_div(s.k, 128), 128, 0, st>>>(
+        left_srht_combine_kernel<T><<<(unsigned)ceil_div(s.k, 8), 256, 0, st>>>(
             (const T *)stage, s.N1, s.d2, s.sample_i1, s.sample_slot, s.k, m, scale, y);
         RHQR_LAUNCH_CHECK();
       } else {
@@ -610,7 +610,7 @@ static rhqr_status arnoldi_reflect(ArnoldiState &a, const T *w, double *h, rhqr_
     left_refresh_kernel<T><<<gr, 256, 0, st>>>(ca);
     RHQR_LAUNCH_CHECK();
     RHQR_TRY(column_srht<T>(ca, a.view, (T *)a.stage, (unsigned)B, st));
-    left_srht_combine_kernel<T><<<dim3((unsigned)ceil_div(a.view.k, 128), (unsigned)B), 128, 0, st>>>(
+    left_srht_combine_kernel<T><<<dim3((unsigned)ceil_div(a.view.k, 8), (unsigned)B), 256, 0, st>>>(
         (const T *)a.stage, a.view.N1, a.view.d2, a.view.sample_i1, a.view.sample_slot, a.view.k, M, scale, a.y,
         a.stage_elems, p);
     RHQR_LAUNCH_CHECK();

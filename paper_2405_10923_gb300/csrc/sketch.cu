@@ -109,22 +109,25 @@ static rhqr_status launch_stage_a_fwht(dim3 grid, const T *X, int64_t ldx, int64
   return RHQR_OK;
 }
 
-// SRHT stage B: Z[m + r, col] = (1/sqrt k) sum_{j1} (-1)^popc(i1_r & j1) Y[col, j1, slot_r]
+// SRHT stage B: Z[m + r, col] = (1/sqrt k) sum_{j1} (-1)^popc(i1_r & j1) Y[col, j1, slot_r],
+// one warp per sampled row (lane l adds j1 = l, l + 32, ...; fixed-order tree).
 template <class T>
 __global__ void srht_stage_b_kernel(const T *Y, int32_t N1, int32_t d2, const int32_t *sample_i1,
                                     const int32_t *sample_slot, int32_t k, int32_t m, double scale, double *Z,
                                     int64_t ldz) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  int col = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int col = blockIdx.y;
   if (r >= k) return;
-  int i1 = sample_i1[r], slot = sample_slot[r];
+  const int i1 = sample_i1[r], slot = sample_slot[r];
   const T *y = Y + (int64_t)col * N1 * d2 + slot;
   double acc = 0.0;
-  for (int j1 = 0; j1 < N1; ++j1) {
-    double t = to_f64<T>(y[(int64_t)j1 * d2]);
+  for (int j1 = lane; j1 < N1; j1 += 32) {
+    const double t = to_f64<T>(y[(int64_t)j1 * d2]);
     acc += (__popc(i1 & j1) & 1) ? -t : t;
   }
-  Z[(int64_t)col * ldz + m + r] = acc * scale;
+  acc = warp_sum(acc);
+  if (lane == 0) Z[(int64_t)col * ldz + m + r] = acc * scale;
 }
 
 // ---------------------------------------------------------------------------
@@ -249,8 +252,8 @@ static rhqr_status apply_typed(const SketchView &s, int32_t m, const TX *X, int6
         RHQR_LAUNCH_CHECK();
       }
     }
-    dim3 gb((unsigned)ceil_div(s.k, 128), c);
-    srht_stage_b_kernel<TX><<<gb, 128, 0, st>>>(Y, s.N1, s.d2, s.sample_i1, s.sample_slot, s.k, m,
+    dim3 gb((unsigned)ceil_div(s.k, 8), c);
+    srht_stage_b_kernel<TX><<<gb, 256, 0, st>>>(Y, s.N1, s.d2, s.sample_i1, s.sample_slot, s.k, m,
                                                  1.0 / sqrt((double)s.k), Z, ldz);
     RHQR_LAUNCH_CHECK();
     return RHQR_OK;

@@ -345,7 +345,7 @@ static rhqr_status trim_typed(const SketchView &s, const T *W, int64_t n, int32_
       left_refresh_kernel<T><<<grid, 256, 0, st>>>(ca);
       RHQR_LAUNCH_CHECK();
       RHQR_TRY(column_srht<T>(ca, s, (T *)stage, 1, st));
-      left_srht_combine_kernel<T><<<(unsigned)ceil_div(k, 128), 128, 0, st>>>(
+      left_srht_combine_kernel<T><<<(unsigned)ceil_div(k, 8), 256, 0, st>>>(
           (const T *)stage, s.N1, s.d2, s.sample_i1, s.sample_slot, k, 0, scale, zw);
       RHQR_LAUNCH_CHECK();
     } else {

@@ -23,7 +23,8 @@ def main():
     ap.add_argument("--m", type=int, default=256)
     ap.add_argument("--k", type=int, default=1024)
     ap.add_argument("--cond", type=float, default=1e10)
-    ap.add_argument("--alg", choices=["rec", "left"], default="rec")
+    ap.add_argument("--alg", choices=["rec", "left", "block"], default="rec")
+    ap.add_argument("--block-size", type=int, default=32)
     ap.add_argument("--passes", type=int, default=1)
     ap.add_argument("--limbs", type=int, nargs=2, default=[2, 2])
     ap.add_argument("--kind", choices=["gaussian", "srht"], default="gaussian")
@@ -44,8 +45,9 @@ def main():
     kind = rh.GAUSSIAN if a.kind == "gaussian" else rh.SRHT
     sdt = {"f64": rh.F64, "f32": rh.F32, "bf16": rh.BF16, "f16": rh.F16}[a.sketch_dtype]
     sk = ta.Sketch(a.n, a.k, kind, 2003, sdt)
-    alg = rh.ALG_REC if a.alg == "rec" else rh.ALG_LEFT
-    opts = ta.make_opts(alg=alg, passes=a.passes, limbs_first=a.limbs[0], limbs_refine=a.limbs[1])
+    alg = {"rec": rh.ALG_REC, "left": rh.ALG_LEFT, "block": rh.ALG_BLOCK}[a.alg]
+    opts = ta.make_opts(alg=alg, passes=a.passes, limbs_first=a.limbs[0], limbs_refine=a.limbs[1],
+                        block_size=a.block_size)
     out = ta.factor(sk, W, opts=opts)
     for _ in range(a.reps - 1):
         rh.rhqr_profile_enable(True)
