@@ -62,24 +62,32 @@ __global__ void left_tcol_coef_kernel(double *T, int32_t m, int32_t j, const dou
   v += (int64_t)blockIdx.x * bs_vec;
   c += (int64_t)blockIdx.x * bs_vec;
   if (j >= 0) {
-    double bj = beta[j];
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    // t_i = -beta_j sum_{l=i}^{j-1} T(i, l) d_l: one warp per row i, lanes over
+    // l (the loads of all warps in flight together), fixed-order warp tree
+    const double bj = beta[j];
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x >> 5; i < m; i += nw) {
       double val = 0.0;
       if (i >= lo && i < j) {
-        for (int l = i; l < j; ++l) val += T[(int64_t)l * m + i] * d[l - lo];
-        val = -bj * val;
+        double acc = 0.0;
+        for (int l = i + lane; l < j; l += 32) acc += T[(int64_t)l * m + i] * d[l - lo];
+        val = -bj * warp_sum(acc);
       } else if (i == j) {
         val = bj;
       }
-      T[(int64_t)j * m + i] = val;
+      if (lane == 0) T[(int64_t)j * m + i] = val;
     }
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+  // c_t = sum_{i=lo}^{l} T(i, l) v_{i-lo}, l = lo + t: one warp per t, the
+  // lanes reading column l of T (coalesced), fixed-order warp tree
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int t = threadIdx.x >> 5; t < nc; t += nw) {
     const int l = lo + t;
     double acc = 0.0;
-    for (int i = lo; i <= l; ++i) acc += T[(int64_t)l * m + i] * v[i - lo];
-    c[t] = acc;
+    for (int i = lo + lane; i <= l; i += 32) acc += T[(int64_t)l * m + i] * v[i - lo];
+    acc = warp_sum(acc);
+    if (lane == 0) c[t] = acc;
   }
 }
 
@@ -202,7 +210,7 @@ static rhqr_status left_typed(const SketchView &s, const T *W, int64_t n, int32_
       dim3 g((unsigned)j, 2);
       left_dots_kernel<<<g, 256, 0, st>>>(S, lds, p, j - 1, j - 1, Zraw + (int64_t)j * p, j, dbuf, vbuf, 0);
       RHQR_LAUNCH_CHECK();
-      left_tcol_coef_kernel<<<1, 256, 0, st>>>(Tm, m, j - 1, beta, dbuf, vbuf, j, cbuf, 0);
+      left_tcol_coef_kernel<<<1, 1024, 0, st>>>(Tm, m, j - 1, beta, dbuf, vbuf, j, cbuf, 0);
       RHQR_LAUNCH_CHECK();
     }
     ca.j = j;
@@ -249,7 +257,7 @@ static rhqr_status left_typed(const SketchView &s, const T *W, int64_t n, int32_
     dim3 g((unsigned)std::max(1, m - 1), 2);
     left_dots_kernel<<<g, 256, 0, st>>>(S, lds, p, m - 1, m - 1, Zraw, 0, dbuf, vbuf, 0);
     RHQR_LAUNCH_CHECK();
-    left_tcol_coef_kernel<<<1, 256, 0, st>>>(Tm, m, m - 1, beta, dbuf, vbuf, 0, cbuf, 0);
+    left_tcol_coef_kernel<<<1, 1024, 0, st>>>(Tm, m, m - 1, beta, dbuf, vbuf, 0, cbuf, 0);
     RHQR_LAUNCH_CHECK();
     left_scale_last_kernel<T><<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(U, ldu, n, m - 1, gam, scaling == 0);
     RHQR_LAUNCH_CHECK();
@@ -415,7 +423,7 @@ static rhqr_status block_typed(const SketchView &s, const T *W, int64_t n, int32
         left_dots_kernel<<<g, 256, 0, st>>>(S, lds, p, j - 1, j - 1 - c0, Zraw + (int64_t)j * p, j - c0, dbuf, vbuf,
                                             c0);
         RHQR_LAUNCH_CHECK();
-        left_tcol_coef_kernel<<<1, 256, 0, st>>>(Tm, m, j - 1, beta, dbuf, vbuf, j - c0, cbuf, c0);
+        left_tcol_coef_kernel<<<1, 1024, 0, st>>>(Tm, m, j - 1, beta, dbuf, vbuf, j - c0, cbuf, c0);
         RHQR_LAUNCH_CHECK();
       }
       ca.j = j;
@@ -461,7 +469,7 @@ static rhqr_status block_typed(const SketchView &s, const T *W, int64_t n, int32
       dim3 g((unsigned)std::max(1, nb - 1), 2);
       left_dots_kernel<<<g, 256, 0, st>>>(S, lds, p, c1 - 1, nb - 1, Zraw, 0, dbuf, vbuf, c0);
       RHQR_LAUNCH_CHECK();
-      left_tcol_coef_kernel<<<1, 256, 0, st>>>(Tm, m, c1 - 1, beta, dbuf, vbuf, 0, cbuf, c0);
+      left_tcol_coef_kernel<<<1, 1024, 0, st>>>(Tm, m, c1 - 1, beta, dbuf, vbuf, 0, cbuf, c0);
       RHQR_LAUNCH_CHECK();
       left_scale_last_kernel<T><<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(U, ldu, n, c1 - 1, gam, scaling == 0);
       RHQR_LAUNCH_CHECK();
@@ -508,11 +516,13 @@ __global__ void arnoldi_coef_kernel(const double *T, int32_t M, const double *S,
   S += b * bs_S;
   gamma += b * M;
   coef += b * M;
-  for (int l = threadIdx.x; l <= j; l += blockDim.x) {
+  // one warp per l, lanes over i (fixed-order warp tree)
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int l = threadIdx.x >> 5; l <= j; l += nw) {
     double acc = 0.0;
-    for (int i = l; i <= j; ++i) acc += T[(int64_t)i * M + l] * S[(int64_t)i * lds + j];
-    if (l == j) acc = acc / gamma[j];
-    coef[l] = acc;
+    for (int i = l + lane; i <= j; i += 32) acc += T[(int64_t)i * M + l] * S[(int64_t)i * lds + j];
+    acc = warp_sum(acc);
+    if (lane == 0) coef[l] = l == j ? acc / gamma[j] : acc;
   }
 }
 
@@ -589,7 +599,7 @@ static rhqr_status arnoldi_tcol(ArnoldiState &a, cudaStream_t st) {
   dim3 g((unsigned)std::max(1, J), 2, (unsigned)B);
   left_dots_kernel<<<g, 256, 0, st>>>(a.S, a.lds, p, J, J, a.z, 0, a.d, a.v, 0, a.lds * M, p, M);
   RHQR_LAUNCH_CHECK();
-  left_tcol_coef_kernel<<<(unsigned)B, 256, 0, st>>>(a.T, M, J, a.beta, a.d, a.v, 0, a.c, 0, (int64_t)M * M, M);
+  left_tcol_coef_kernel<<<(unsigned)B, 1024, 0, st>>>(a.T, M, J, a.beta, a.d, a.v, 0, a.c, 0, (int64_t)M * M, M);
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }
@@ -653,7 +663,7 @@ static rhqr_status arnoldi_reflect(ArnoldiState &a, const T *w, double *h, rhqr_
 template <class T>
 static rhqr_status arnoldi_basis(ArnoldiState &a, T *q, cudaStream_t st) {
   const int32_t J = a.j - 1, B = a.nrhs;
-  arnoldi_coef_kernel<<<(unsigned)B, 256, 0, st>>>(a.T, a.M, a.S, a.lds, J, a.gamma, a.coef, a.lds * a.M);
+  arnoldi_coef_kernel<<<(unsigned)B, 1024, 0, st>>>(a.T, a.M, a.S, a.lds, J, a.gamma, a.coef, a.lds * a.M);
   RHQR_LAUNCH_CHECK();
   arnoldi_q_kernel<T><<<dim3((unsigned)ceil_div(a.n, 256), (unsigned)B), 256, 0, st>>>(
       (const T *)a.U, a.ldu, a.n, J, a.coef, q, a.ldu * a.M, a.M);
@@ -682,7 +692,7 @@ static rhqr_status arnoldi_step_t(ArnoldiState &a, const T *w, double *h, T *qn,
   dim3 g((unsigned)J, 2, (unsigned)B);
   left_dots_kernel<<<g, 256, 0, st>>>(a.S, a.lds, p, 0, 0, a.z, J, a.d, a.v, 0, a.lds * M, p, M);
   RHQR_LAUNCH_CHECK();
-  left_tcol_coef_kernel<<<(unsigned)B, 256, 0, st>>>(a.T, M, -1, a.beta, a.d, a.v, J, a.c, 0, (int64_t)M * M, M);
+  left_tcol_coef_kernel<<<(unsigned)B, 1024, 0, st>>>(a.T, M, -1, a.beta, a.d, a.v, J, a.c, 0, (int64_t)M * M, M);
   RHQR_LAUNCH_CHECK();
   RHQR_TRY(arnoldi_reflect<T>(a, w, h, info, st));
   if (qn != nullptr) RHQR_TRY(arnoldi_basis<T>(a, qn, st));

@@ -93,10 +93,12 @@ static __global__ void trim_coef_kernel(const double *S, int64_t lds, int32_t k,
     if (lane == 0) v[i] = acc - low;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < j; t += blockDim.x) {
+  // c_t = sum_{i<=t} Tt(i, t) v_i: one warp per t, lanes reading column t (coalesced)
+  for (int t = wid; t < j; t += nw) {
     double acc = 0.0;
-    for (int i = 0; i <= t; ++i) acc += Tt[(int64_t)t * m + i] * v[i];
-    c[t] = acc;
+    for (int i = lane; i <= t; i += 32) acc += Tt[(int64_t)t * m + i] * v[i];
+    acc = warp_sum(acc);
+    if (lane == 0) c[t] = acc;
   }
 }
 
@@ -195,28 +197,32 @@ static __global__ void trim_tcol_kernel(const double *S, int64_t lds, int32_t k,
   }
   __syncthreads();
   // d2_l = d1_l - sum_{i<j} Utop(i, l) L(j, i)   (Utop(i, l) = 0 for i < l)
-  for (int l = threadIdx.x; l < j; l += blockDim.x) {
-    double acc = d1[l];
-    for (int i = l; i < j; ++i) acc -= Utop[(int64_t)l * m + i] * L[(int64_t)i * m + j];
-    d2[l] = acc;
+  for (int l = wid; l < j; l += nw) {  // one warp per l, lanes over i (Utop column l, coalesced)
+    double acc = 0.0;
+    for (int i = l + lane; i < j; i += 32) acc += Utop[(int64_t)l * m + i] * L[(int64_t)i * m + j];
+    acc = warp_sum(acc);
+    if (lane == 0) d2[l] = d1[l] - acc;
   }
   __syncthreads();
   const double bj = beta[j];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+  // one warp per row i, lanes over l, fixed-order warp trees
+  for (int i = wid; i < m; i += nw) {
     double tv = 0.0, ttv = 0.0;
     if (i < j) {
-      for (int l = i; l < j; ++l) {
+      for (int l = i + lane; l < j; l += 32) {
         tv += T[(int64_t)l * m + i] * d1[l];
         ttv += Tt[(int64_t)l * m + i] * d2[l];
       }
-      tv = -bj * tv;
-      ttv = -bj * ttv;
+      tv = -bj * warp_sum(tv);
+      ttv = -bj * warp_sum(ttv);
     } else if (i == j) {
       tv = bj;
       ttv = bj;
     }
-    T[(int64_t)j * m + i] = tv;
-    Tt[(int64_t)j * m + i] = ttv;
+    if (lane == 0) {
+      T[(int64_t)j * m + i] = tv;
+      Tt[(int64_t)j * m + i] = ttv;
+    }
   }
 }
 
@@ -337,7 +343,7 @@ static rhqr_status trim_typed(const SketchView &s, const T *W, int64_t n, int32_
   ColArgs ca{W, ldw, U, ldu, n, m, 0, cbuf, gam, x, scaling == 0 ? 1 : 0, 0, 0};
   for (int32_t j = 0; j < m; ++j) {
     if (j >= 1) {
-      trim_coef_kernel<<<1, 256, 0, st>>>(S, lds, k, j, Zraw + (int64_t)j * k, L, m, xin + (int64_t)j * m, Tt, cbuf);
+      trim_coef_kernel<<<1, 1024, 0, st>>>(S, lds, k, j, Zraw + (int64_t)j * k, L, m, xin + (int64_t)j * m, Tt, cbuf);
       RHQR_LAUNCH_CHECK();
     }
     ca.j = j;
@@ -376,7 +382,7 @@ static rhqr_status trim_typed(const SketchView &s, const T *W, int64_t n, int32_
     trim_vector_kernel<T><<<1, 256, 0, st>>>(zw, E, nrm, k, m, j, x, scaling, S, lds, R, beta, gam, U, ldu, Utop, L,
                                              zbuf, info, stop);
     RHQR_LAUNCH_CHECK();
-    trim_tcol_kernel<<<1, 256, 0, st>>>(S, lds, k, m, j, beta, Utop, L, Tm, Tt, stop);
+    trim_tcol_kernel<<<1, 1024, 0, st>>>(S, lds, k, m, j, beta, Utop, L, Tm, Tt, stop);
     RHQR_LAUNCH_CHECK();
   }
   left_scale_last_kernel<T><<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(U, ldu, n, m - 1, gam, scaling == 0);
