@@ -14,6 +14,7 @@
 // small matrices are read transposed (row l contiguous) and padded to a
 // multiple of 32 with an identity, so panels need no bounds checks.
 #include "apply.cuh"
+#include "solve_inv_tc.cuh"
 #include "common.cuh"
 
 namespace rhqr {
@@ -204,6 +205,36 @@ rhqr_status top_from_s(const double *S, int64_t lds, int32_t m, T *U, int64_t ld
   return RHQR_OK;
 }
 
+// Q = [I_m; 0] - U G for an upper-triangular G (m x m float64, ld m; G is
+// overwritten).  float32 with m <= 256: on the tensor cores as the product
+// with -G (rows_solve_inv_tc, the explicit-inverse solve, whose operand is an
+// upper-triangular matrix with a nonzero diagonal: here diag(G)_j = t_jj
+// u_jj != 0), then the identity block added; otherwise the SIMT row pass.
+static __global__ void negate_kernel(double *A, int64_t count) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) A[e] = -A[e];
+}
+template <class T>
+static __global__ void add_identity_kernel(T *Q, int64_t ldq, int32_t m) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < m) Q[(int64_t)j * ldq + j] += T(1);
+}
+
+template <class T>
+rhqr_status form_q_from_g(const T *U, int64_t ldu, int64_t n, int32_t m, double *Gm, void *GT, T *Q, int64_t ldq,
+                          rhqr_info *info, cudaStream_t st) {
+  if (sizeof(T) == 4 && solve_inv_tc_supported(m) && (const void *)U != (const void *)Q) {
+    negate_kernel<<<(unsigned)ceil_div((int64_t)m * m, 256), 256, 0, st>>>(Gm, (int64_t)m * m);
+    RHQR_LAUNCH_CHECK();
+    RHQR_TRY(rows_solve_inv_tc((const float *)U, ldu, n, m, Gm, 0, (float *)Q, ldq, info, kDefaultWaitBudget, st));
+    add_identity_kernel<T><<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(Q, ldq, m);
+    RHQR_LAUNCH_CHECK();
+    return RHQR_OK;
+  }
+  RHQR_TRY(pad_transpose<T>(Gm, m, 1, (T *)GT, st));
+  return rows_form_q<T>(U, ldu, 0, n, m, (const T *)GT, Q, ldq, st);
+}
+
 #define RHQR_INST(T)                                                                                          \
   template rhqr_status rows_solve<T>(const T *, int64_t, int64_t, int64_t, int32_t, const T *, T *, int64_t,  \
                                      cudaStream_t);                                                           \
@@ -211,7 +242,9 @@ rhqr_status top_from_s(const double *S, int64_t lds, int32_t m, T *U, int64_t ld
                                          T *, int64_t, T *, int64_t, cudaStream_t);                           \
   template rhqr_status rows_form_q<T>(const T *, int64_t, int64_t, int64_t, int32_t, const T *, T *, int64_t, \
                                       cudaStream_t);                                                          \
-  template rhqr_status top_from_s<T>(const double *, int64_t, int32_t, T *, int64_t, cudaStream_t);
+  template rhqr_status top_from_s<T>(const double *, int64_t, int32_t, T *, int64_t, cudaStream_t);          \
+  template rhqr_status form_q_from_g<T>(const T *, int64_t, int64_t, int32_t, double *, void *, T *, int64_t,   \
+                                        rhqr_info *, cudaStream_t);
 RHQR_INST(float)
 RHQR_INST(double)
 #undef RHQR_INST

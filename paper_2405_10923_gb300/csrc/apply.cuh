@@ -25,6 +25,12 @@ rhqr_status rows_solve_mul(const T *X, int64_t ldx, int64_t row_begin, int64_t n
 template <class T>
 rhqr_status rows_form_q(const T *U, int64_t ldu, int64_t row_begin, int64_t nrows, int32_t m, const T *GT, T *Q,
                         int64_t ldq, cudaStream_t st);
+// Q = [I_m; 0] - U G (G upper triangular, m x m float64, overwritten; GT:
+// small_padded_bytes(m) of scratch): tensor cores for float32 and m <= 256,
+// else the row pass.  A tensor-core wait that ran out is reported in info.
+template <class T>
+rhqr_status form_q_from_g(const T *U, int64_t ldu, int64_t n, int32_t m, double *Gm, void *GT, T *Q, int64_t ldq,
+                          rhqr_info *info, cudaStream_t st);
 // U[0:m, :] = S[0:m, :]
 template <class T>
 rhqr_status top_from_s(const double *S, int64_t lds, int32_t m, T *U, int64_t ldu, cudaStream_t st);

@@ -265,8 +265,7 @@ static rhqr_status left_typed(const SketchView &s, const T *W, int64_t n, int32_
   if (Q != nullptr) {
     // Q = [I; 0] - U (T U_1^t)  (Section 3.2)
     RHQR_TRY(t_u1t(Tm, S, lds, m, Gm, st));
-    RHQR_TRY(pad_transpose<T>(Gm, m, 1, (T *)GT, st));
-    RHQR_TRY(rows_form_q<T>(U, ldu, 0, n, m, (const T *)GT, Q, ldq, st));
+    RHQR_TRY(form_q_from_g<T>(U, ldu, n, m, Gm, GT, Q, ldq, info, st));
   }
   return RHQR_OK;
 }
@@ -480,8 +479,7 @@ static rhqr_status block_typed(const SketchView &s, const T *W, int64_t n, int32
   RHQR_TRY(t_factor_small(S, lds, p, m, beta, SS, Tm, st));
   if (Q != nullptr) {
     RHQR_TRY(t_u1t(Tm, S, lds, m, Gm, st));
-    RHQR_TRY(pad_transpose<T>(Gm, m, 1, (T *)GT, st));
-    RHQR_TRY(rows_form_q<T>(U, ldu, 0, n, m, (const T *)GT, Q, ldq, st));
+    RHQR_TRY(form_q_from_g<T>(U, ldu, n, m, Gm, GT, Q, ldq, info, st));
   }
   return RHQR_OK;
 }

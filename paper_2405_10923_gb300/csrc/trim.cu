@@ -390,6 +390,8 @@ static rhqr_status trim_typed(const SketchView &s, const T *W, int64_t n, int32_
   if (Q != nullptr) {
     trim_g_kernel<<<m, 256, 0, st>>>(Tm, S, lds, k, m, E, Gm);
     RHQR_LAUNCH_CHECK();
+    // (the row pass: G's diagonal beta_j (s_j . E_j) has no bound away from zero,
+    // which the tensor-core product with -G would need)
     RHQR_TRY(pad_transpose<T>(Gm, m, 1, (T *)GT, st));
     RHQR_TRY(rows_form_q<T>(U, ldu, 0, n, m, (const T *)GT, Q, ldq, st));
   }
