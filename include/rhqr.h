@@ -154,6 +154,28 @@ rhqr_status rhqr_sketch_apply(rhqr_sketch s, int32_t m, const void *X, int32_t x
                               size_t ws_bytes, rhqr_stream_t stream);
 
 /*
+ * rhqr_sketch_apply_rows -- one row shard's share of Algorithm 1 for a matrix
+ * distributed by rows (each holder sketches its own rows, one sum of the
+ * (k+m) x c results gives Z = Psi_m X; the paper's single synchronization):
+ *   Z = Psi_m[:, row0 : row0+rows] X_local,
+ * X_local (rows x c, dtype xt = F64 or F32, ldx >= rows) holding the global
+ * rows row0 .. row0+rows-1 of an n-row X (n = the sketch's n).  The top block
+ * of Z holds the shard's rows among the first m (zero elsewhere); the bottom k
+ * rows the shard's columns of Omega applied to its rows >= m.  Gaussian: the
+ * columns row0.. of Omega_full.  SRHT: the shard's segments of the Kronecker
+ * split H_N = H_{N/N2} (x) H_{N2} transformed locally and combined with the
+ * global segment signs; row0 must be a multiple of the segment length N2 =
+ * min(N, 8192) (RHQR_EINVAL otherwise).  The float64 sums of the shards equal
+ * rhqr_sketch_apply's Z to rounding.  ws: rhqr_sketch_apply_rows_workspace
+ * bytes.  Requires 0 <= m <= k, m < n, 0 <= row0, row0 + rows <= n.
+ */
+rhqr_status rhqr_sketch_apply_rows_workspace(rhqr_sketch s, int32_t m, int32_t xt, int64_t row0, int64_t rows,
+                                             int32_t c, size_t *bytes);
+rhqr_status rhqr_sketch_apply_rows(rhqr_sketch s, int32_t m, const void *X, int32_t xt, int64_t row0, int64_t rows,
+                                   int32_t c, int64_t ldx, double *Z, int64_t ldz, void *ws, size_t ws_bytes,
+                                   rhqr_stream_t stream);
+
+/*
  * rhqr_factor -- randomized Householder QR of W (n x m, dtype wt = F64 or F32).
  *  alg = RHQR_ALG_LEFT: Algorithm 4 (left-looking RHQR): column j is refreshed
  *        with the previous reflectors, w_j <- w_j - U T^t S^t Psi w_j, sketched,

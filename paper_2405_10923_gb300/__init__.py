@@ -87,6 +87,8 @@ _SIGNATURES = {
     "rhqr_sketch_apply_workspace": (_i32, [_p, _i32, _i32, _i64, _i32, ctypes.POINTER(_sz)]),
     "rhqr_workspace_size": (_i32, [_p, _i64, _i32, _i32, ctypes.POINTER(rhqr_opts), ctypes.POINTER(_sz)]),
     "rhqr_sketch_apply": (_i32, [_p, _i32, _p, _i32, _i64, _i32, _i64, _p, _i64, _p, _sz, _p]),
+    "rhqr_sketch_apply_rows_workspace": (_i32, [_p, _i32, _i32, _i64, _i64, _i32, ctypes.POINTER(_sz)]),
+    "rhqr_sketch_apply_rows": (_i32, [_p, _i32, _p, _i32, _i64, _i64, _i32, _i64, _p, _i64, _p, _sz, _p]),
     "rhqr_factor": (_i32, [_p, _p, _i32, _i64, _i32, _i64, ctypes.POINTER(rhqr_opts), _p, _i64, _p, _i64, _p, _p,
                            _p, _i64, _p, _sz, _p, _p]),
     "rhqr_reconstruct": (_i32, [_p, _p, _i64, _p, _p, _p, _i64, _p, _i32, _i64, _i32, _i64, _p, _i64, _p, _i64, _p,
@@ -336,6 +338,18 @@ def rhqr_blas2_rgs_workspace(s, wt, n, m) -> int:
 def rhqr_blas2_rgs(s, W, wt, n, m, ldw, Q, ldq, R, T, S, ws, ws_bytes, info, stream=None) -> None:
     _check("rhqr_blas2_rgs", load().rhqr_blas2_rgs(s, _ptr(W), wt, n, m, ldw, _ptr(Q), ldq, _ptr(R), _ptr(T), _ptr(S),
                                                    _ptr(ws), ws_bytes, _ptr(info), _stream(stream)))
+
+
+def rhqr_sketch_apply_rows_workspace(s, m, xt, row0, rows, c) -> int:
+    out = _sz()
+    _check("rhqr_sketch_apply_rows_workspace",
+           load().rhqr_sketch_apply_rows_workspace(s, m, xt, row0, rows, c, ctypes.byref(out)))
+    return out.value
+
+
+def rhqr_sketch_apply_rows(s, m, X, xt, row0, rows, c, ldx, Z, ldz, ws, ws_bytes, stream=None) -> None:
+    _check("rhqr_sketch_apply_rows", load().rhqr_sketch_apply_rows(s, m, _ptr(X), xt, row0, rows, c, ldx, _ptr(Z), ldz,
+                                                                   _ptr(ws), ws_bytes, _stream(stream)))
 
 
 def rhqr_trim_workspace(s, wt, n, m) -> int:

@@ -273,6 +273,31 @@ rhqr_status rhqr_sketch_apply(rhqr_sketch s, int32_t m, const void *X, int32_t x
   return sketch_apply_simt(s->view, m, X, xt, n, c, ldx, Z, ldz, ws, ws_bytes, (cudaStream_t)stream);
 }
 
+static rhqr_status check_rows(const SketchView &v, int32_t m, int32_t xt, int64_t row0, int64_t rows, int32_t c) {
+  if (!valid_dtype_hd(xt) || c < 1 || rows < 1 || row0 < 0 || m < 0 || m > v.k || m >= v.n) return RHQR_EINVAL;
+  if (row0 + rows > v.n) return RHQR_EINVAL;
+  if (v.kind == RHQR_SKETCH_SRHT && row0 % v.N2 != 0) return RHQR_EINVAL;  // shards start on a segment
+  return RHQR_OK;
+}
+
+rhqr_status rhqr_sketch_apply_rows_workspace(rhqr_sketch s, int32_t m, int32_t xt, int64_t row0, int64_t rows,
+                                             int32_t c, size_t *bytes) {
+  if (s == nullptr || bytes == nullptr) return RHQR_EINVAL;
+  RHQR_TRY(check_rows(s->view, m, xt, row0, rows, c));
+  *bytes = sketch_rows_workspace_bytes(s->view, m, xt, row0, rows, c);
+  return RHQR_OK;
+}
+
+rhqr_status rhqr_sketch_apply_rows(rhqr_sketch s, int32_t m, const void *X, int32_t xt, int64_t row0, int64_t rows,
+                                   int32_t c, int64_t ldx, double *Z, int64_t ldz, void *ws, size_t ws_bytes,
+                                   rhqr_stream_t stream) {
+  if (s == nullptr || X == nullptr || Z == nullptr) return RHQR_EINVAL;
+  RHQR_TRY(check_rows(s->view, m, xt, row0, rows, c));
+  if (ldx < rows || ldz < (int64_t)s->view.k + m) return RHQR_EINVAL;
+  if (ws == nullptr || ws_bytes < sketch_rows_workspace_bytes(s->view, m, xt, row0, rows, c)) return RHQR_ENOMEM;
+  return sketch_apply_rows_simt(s->view, m, X, xt, row0, rows, c, ldx, Z, ldz, ws, ws_bytes, (cudaStream_t)stream);
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

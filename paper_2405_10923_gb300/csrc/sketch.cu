@@ -34,19 +34,27 @@ __global__ void copy_top_kernel(const T *X, int64_t ldx, int32_t m, int32_t c, d
 // column (rows < m and >= n read as zero, signs applied) and writes the values
 // at the d2 sampled in-block positions to Y[(col * N1 + j1) * d2 + slot].
 // ---------------------------------------------------------------------------
+// Rows of the column held by X: global rows [first, end) at X[i - first], in
+// the segments seg0, seg0 + 1, ... (the whole column: first 0, end n, seg0 0;
+// a row shard of a distributed matrix: its own rows and segments).
+struct RowWindow {
+  int64_t first, end;
+  int32_t seg0;
+};
+
 template <class T>
-__global__ void srht_stage_a_kernel(const T *X, int64_t ldx, int64_t n, int32_t m, const uint32_t *sign_bits,
+__global__ void srht_stage_a_kernel(const T *X, int64_t ldx, RowWindow win, int32_t m, const uint32_t *sign_bits,
                                     int32_t N2, int32_t N1, const int32_t *i2_list, int32_t d2, T *Y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *v = reinterpret_cast<T *>(smem_raw);
   const int j1 = blockIdx.x, col = blockIdx.y;
   const T *x = X + (int64_t)col * ldx;
-  const int64_t row0 = (int64_t)j1 * N2;
+  const int64_t row0 = (int64_t)(win.seg0 + j1) * N2;
   for (int t = threadIdx.x; t < N2; t += blockDim.x) {
     int64_t i = row0 + t;
     T val = T(0);
-    if (i >= m && i < n) {
-      val = x[i];
+    if (i >= m && i >= win.first && i < win.end) {
+      val = x[i - win.first];
       if ((sign_bits[i >> 5] >> (i & 31)) & 1u) val = -val;
     }
     v[t] = val;
@@ -70,7 +78,7 @@ __global__ void srht_stage_a_kernel(const T *X, int64_t ldx, int64_t n, int32_t 
 // zero rows applied on the way), transformed by fwht_segment, the sampled
 // in-block positions written out.
 template <class T, int LOGN2>
-__global__ void __launch_bounds__(1 << (LOGN2 - 4)) srht_stage_a_fwht_kernel(const T *X, int64_t ldx, int64_t n,
+__global__ void __launch_bounds__(1 << (LOGN2 - 4)) srht_stage_a_fwht_kernel(const T *X, int64_t ldx, RowWindow win,
                                                                              int32_t m, const uint32_t *sign_bits,
                                                                              int32_t N1, const int32_t *i2_list,
                                                                              int32_t d2, T *Y) {
@@ -79,14 +87,14 @@ __global__ void __launch_bounds__(1 << (LOGN2 - 4)) srht_stage_a_fwht_kernel(con
   T *buf = reinterpret_cast<T *>(smem_raw);
   const int j1 = blockIdx.x, col = blockIdx.y, t = threadIdx.x;
   const T *x = X + (int64_t)col * ldx;
-  const int64_t row0 = (int64_t)j1 * N2;
+  const int64_t row0 = (int64_t)(win.seg0 + j1) * N2;
   T v[16];
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
     const int64_t i = row0 + r * NT + t;
     T val = T(0);
-    if (i >= m && i < n) {
-      val = x[i];
+    if (i >= m && i >= win.first && i < win.end) {
+      val = x[i - win.first];
       if ((sign_bits[i >> 5] >> (i & 31)) & 1u) val = -val;
     }
     v[r] = val;
@@ -97,13 +105,13 @@ __global__ void __launch_bounds__(1 << (LOGN2 - 4)) srht_stage_a_fwht_kernel(con
 }
 
 template <class T, int LOGN2>
-static rhqr_status launch_stage_a_fwht(dim3 grid, const T *X, int64_t ldx, int64_t n, int32_t m,
+static rhqr_status launch_stage_a_fwht(dim3 grid, const T *X, int64_t ldx, RowWindow win, int32_t m,
                                        const SketchView &s, T *Y, cudaStream_t st) {
   const size_t smem = sizeof(T) << LOGN2;
   if (smem > 48 * 1024)
     RHQR_CUDA_TRY(cudaFuncSetAttribute(srht_stage_a_fwht_kernel<T, LOGN2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  srht_stage_a_fwht_kernel<T, LOGN2><<<grid, 1 << (LOGN2 - 4), smem, st>>>(X, ldx, n, m, s.sign_bits, s.N1,
+  srht_stage_a_fwht_kernel<T, LOGN2><<<grid, 1 << (LOGN2 - 4), smem, st>>>(X, ldx, win, m, s.sign_bits, grid.x,
                                                                             s.i2_list, s.d2, Y);
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
@@ -114,7 +122,7 @@ static rhqr_status launch_stage_a_fwht(dim3 grid, const T *X, int64_t ldx, int64
 template <class T>
 __global__ void srht_stage_b_kernel(const T *Y, int32_t N1, int32_t d2, const int32_t *sample_i1,
                                     const int32_t *sample_slot, int32_t k, int32_t m, double scale, double *Z,
-                                    int64_t ldz) {
+                                    int64_t ldz, int32_t seg0) {
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int col = blockIdx.y;
@@ -124,7 +132,7 @@ __global__ void srht_stage_b_kernel(const T *Y, int32_t N1, int32_t d2, const in
   double acc = 0.0;
   for (int j1 = lane; j1 < N1; j1 += 32) {
     const double t = to_f64<T>(y[(int64_t)j1 * d2]);
-    acc += (__popc(i1 & j1) & 1) ? -t : t;
+    acc += (__popc(i1 & (seg0 + j1)) & 1) ? -t : t;
   }
   acc = warp_sum(acc);
   if (lane == 0) Z[(int64_t)col * ldz + m + r] = acc * scale;
@@ -227,6 +235,35 @@ size_t sketch_apply_workspace_bytes(const SketchView &s, int32_t m, int32_t xt, 
   return align_up((size_t)nch * s.k * c * sizeof(double), 256) + 256;
 }
 
+// Stage A over the segments seg0 .. seg0 + nseg - 1 of the window's rows,
+// stage B summing them with the global segment signs: Z[m + r, col] for the
+// rows in the window (the whole column, or a shard's share of the sum).
+template <class TX>
+static rhqr_status srht_apply(const SketchView &s, int32_t m, const TX *X, int64_t ldx, RowWindow win, int32_t nseg,
+                              int32_t c, double *Z, int64_t ldz, void *ws, size_t ws_bytes, cudaStream_t st) {
+  TX *Y = (TX *)ws;
+  size_t need = (size_t)c * nseg * s.d2 * sizeof(TX);
+  if (ws_bytes < need) return RHQR_ENOMEM;
+  dim3 ga((unsigned)nseg, c);
+  switch (s.N2) {
+    case 8192: RHQR_TRY((launch_stage_a_fwht<TX, 13>(ga, X, ldx, win, m, s, Y, st))); break;
+    case 4096: RHQR_TRY((launch_stage_a_fwht<TX, 12>(ga, X, ldx, win, m, s, Y, st))); break;
+    case 2048: RHQR_TRY((launch_stage_a_fwht<TX, 11>(ga, X, ldx, win, m, s, Y, st))); break;
+    case 1024: RHQR_TRY((launch_stage_a_fwht<TX, 10>(ga, X, ldx, win, m, s, Y, st))); break;
+    case 512: RHQR_TRY((launch_stage_a_fwht<TX, 9>(ga, X, ldx, win, m, s, Y, st))); break;
+    default: {  // short transforms: one butterfly level per step in shared memory
+      size_t smem = (size_t)s.N2 * sizeof(TX);
+      srht_stage_a_kernel<TX><<<ga, 512, smem, st>>>(X, ldx, win, m, s.sign_bits, s.N2, nseg, s.i2_list, s.d2, Y);
+      RHQR_LAUNCH_CHECK();
+    }
+  }
+  dim3 gb((unsigned)ceil_div(s.k, 8), c);
+  srht_stage_b_kernel<TX><<<gb, 256, 0, st>>>(Y, nseg, s.d2, s.sample_i1, s.sample_slot, s.k, m,
+                                               1.0 / sqrt((double)s.k), Z, ldz, win.seg0);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
+}
+
 template <class TX>
 static rhqr_status apply_typed(const SketchView &s, int32_t m, const TX *X, int64_t n, int32_t c, int64_t ldx,
                                double *Z, int64_t ldz, void *ws, size_t ws_bytes, cudaStream_t st) {
@@ -235,29 +272,7 @@ static rhqr_status apply_typed(const SketchView &s, int32_t m, const TX *X, int6
     copy_top_kernel<TX><<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(X, ldx, m, c, Z, ldz);
     RHQR_LAUNCH_CHECK();
   }
-  if (s.kind == RHQR_SKETCH_SRHT) {
-    TX *Y = (TX *)ws;
-    size_t need = (size_t)c * s.N1 * s.d2 * sizeof(TX);
-    if (ws_bytes < need) return RHQR_ENOMEM;
-    dim3 ga(s.N1, c);
-    switch (s.N2) {
-      case 8192: RHQR_TRY((launch_stage_a_fwht<TX, 13>(ga, X, ldx, n, m, s, Y, st))); break;
-      case 4096: RHQR_TRY((launch_stage_a_fwht<TX, 12>(ga, X, ldx, n, m, s, Y, st))); break;
-      case 2048: RHQR_TRY((launch_stage_a_fwht<TX, 11>(ga, X, ldx, n, m, s, Y, st))); break;
-      case 1024: RHQR_TRY((launch_stage_a_fwht<TX, 10>(ga, X, ldx, n, m, s, Y, st))); break;
-      case 512: RHQR_TRY((launch_stage_a_fwht<TX, 9>(ga, X, ldx, n, m, s, Y, st))); break;
-      default: {  // short transforms: one butterfly level per step in shared memory
-        size_t smem = (size_t)s.N2 * sizeof(TX);
-        srht_stage_a_kernel<TX><<<ga, 512, smem, st>>>(X, ldx, n, m, s.sign_bits, s.N2, s.N1, s.i2_list, s.d2, Y);
-        RHQR_LAUNCH_CHECK();
-      }
-    }
-    dim3 gb((unsigned)ceil_div(s.k, 8), c);
-    srht_stage_b_kernel<TX><<<gb, 256, 0, st>>>(Y, s.N1, s.d2, s.sample_i1, s.sample_slot, s.k, m,
-                                                 1.0 / sqrt((double)s.k), Z, ldz);
-    RHQR_LAUNCH_CHECK();
-    return RHQR_OK;
-  }
+  if (s.kind == RHQR_SKETCH_SRHT) return srht_apply<TX>(s, m, X, ldx, RowWindow{0, n, 0}, s.N1, c, Z, ldz, ws, ws_bytes, st);
   // Gaussian
   int64_t K = n - m;
   int nch = gauss_chunks(K, s.k, c);
@@ -310,6 +325,64 @@ static rhqr_status apply_typed(const SketchView &s, int32_t m, const TX *X, int6
                                                                      Z, ldz);
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
+}
+
+// Top block of a shard's Z: Z[i, col] = X[i - row0, col] for the rows i < m
+// in [row0, row0 + rows), else 0.
+template <class TX>
+__global__ void shard_top_kernel(const TX *X, int64_t ldx, int64_t row0, int64_t rows, int32_t m, int32_t c,
+                                 double *Z, int64_t ldz) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)m * c) return;
+  const int64_t col = idx / m, i = idx - col * m;
+  Z[col * ldz + i] = (i >= row0 && i < row0 + rows) ? to_f64<TX>(X[col * ldx + (i - row0)]) : 0.0;
+}
+
+size_t sketch_rows_workspace_bytes(const SketchView &s, int32_t m, int32_t xt, int64_t row0, int64_t rows,
+                                   int32_t c) {
+  if (s.kind == RHQR_SKETCH_SRHT) {
+    const int64_t nseg = ceil_div(rows, s.N2);
+    return align_up((size_t)c * nseg * s.d2 * dtype_size(xt), 256) + 256;
+  }
+  const int32_t ml = (int32_t)std::min<int64_t>(std::max<int64_t>(m - row0, 0), rows);
+  return sketch_apply_workspace_bytes(s, ml, xt, rows, c);
+}
+
+template <class TX>
+static rhqr_status rows_typed(const SketchView &s, int32_t m, const TX *X, int64_t row0, int64_t rows, int32_t c,
+                              int64_t ldx, double *Z, int64_t ldz, void *ws, size_t ws_bytes, cudaStream_t st) {
+  if (s.kind == RHQR_SKETCH_SRHT) {
+    const int32_t nseg = (int32_t)ceil_div(rows, s.N2);
+    RHQR_TRY(srht_apply<TX>(s, m, X, ldx, RowWindow{row0, row0 + rows, (int32_t)(row0 / s.N2)}, nseg, c, Z, ldz, ws,
+                            ws_bytes, st));
+  } else {
+    // the shard's columns of Omega_full: the operator seen from column row0
+    SketchView v = s;
+    v.G = (const char *)s.G + (size_t)row0 * dtype_size(s.omega_dtype);
+    v.Gt = nullptr;
+    const int32_t ml = (int32_t)std::min<int64_t>(std::max<int64_t>(m - row0, 0), rows);
+    if (ml < rows) {
+      // Z rows m .. m + k - 1 from the shard's rows ml .. rows - 1 (global row0 + ml ..)
+      RHQR_TRY(apply_typed<TX>(v, ml, X, rows, c, ldx, Z + (m - ml), ldz, ws, ws_bytes, st));
+    } else {
+      RHQR_CUDA_TRY(cudaMemset2DAsync(Z + m, ldz * sizeof(double), 0, (size_t)s.k * sizeof(double), c, st));
+    }
+  }
+  if (m > 0) {
+    shard_top_kernel<TX><<<(unsigned)ceil_div((int64_t)m * c, 256), 256, 0, st>>>(X, ldx, row0, rows, m, c, Z, ldz);
+    RHQR_LAUNCH_CHECK();
+  }
+  return RHQR_OK;
+}
+
+rhqr_status sketch_apply_rows_simt(const SketchView &s, int32_t m, const void *X, int32_t xt, int64_t row0,
+                                   int64_t rows, int32_t c, int64_t ldx, double *Z, int64_t ldz, void *ws,
+                                   size_t ws_bytes, cudaStream_t st) {
+  if (xt == RHQR_F64)
+    return rows_typed<double>(s, m, (const double *)X, row0, rows, c, ldx, Z, ldz, ws, ws_bytes, st);
+  if (xt == RHQR_F32)
+    return rows_typed<float>(s, m, (const float *)X, row0, rows, c, ldx, Z, ldz, ws, ws_bytes, st);
+  return RHQR_ENOTSUP;
 }
 
 rhqr_status sketch_apply_simt(const SketchView &s, int32_t m, const void *X, int32_t xt, int64_t n, int32_t c,

@@ -27,6 +27,16 @@ struct SketchView {
 
 size_t sketch_apply_workspace_bytes(const SketchView &s, int32_t m, int32_t xt, int64_t n, int32_t c);
 
+// One row shard's share of Z = Psi_m X: Z = Psi_m[:, row0:row0+rows] X_local
+// (X_local: the global rows row0 .. row0 + rows - 1), so that the shards' Z
+// sum to the whole sketch.  SRHT shards start on a segment boundary (row0 a
+// multiple of N2).
+size_t sketch_rows_workspace_bytes(const SketchView &s, int32_t m, int32_t xt, int64_t row0, int64_t rows,
+                                   int32_t c);
+rhqr_status sketch_apply_rows_simt(const SketchView &s, int32_t m, const void *X, int32_t xt, int64_t row0,
+                                   int64_t rows, int32_t c, int64_t ldx, double *Z, int64_t ldz, void *ws,
+                                   size_t ws_bytes, cudaStream_t st);
+
 // Z = Psi_m X with the SIMT kernels (SRHT or Gaussian of any stored dtype).
 rhqr_status sketch_apply_simt(const SketchView &s, int32_t m, const void *X, int32_t xt, int64_t n, int32_t c,
                               int64_t ldx, double *Z, int64_t ldz, void *ws, size_t ws_bytes, cudaStream_t st);

@@ -15,7 +15,8 @@ from . import (ALG_LEFT, ALG_REC, BF16, F16, F32, F64, GAUSSIAN, SRHT, colmajor,
                rhqr_stencil_apply, rhqr_stencil_residual, rhqr_stencil_residual_workspace, rhqr_arnoldi_solution_x, rhqr_arnoldi_destroy, rhqr_arnoldi_export, rhqr_arnoldi_step,
                rhqr_default_opts, rhqr_factor, rhqr_pipeline_create, rhqr_pipeline_destroy, rhqr_pipeline_submit,
                rhqr_pipeline_wait, rhqr_arnoldi_solution, rhqr_blas2_rgs, rhqr_blas2_rgs_workspace, rhqr_reconstruct,
-               rhqr_trim_factor, rhqr_trim_workspace, rhqr_sketch_apply, rhqr_sketch_apply_workspace,
+               rhqr_trim_factor, rhqr_trim_workspace, rhqr_sketch_apply_rows,
+               rhqr_sketch_apply_rows_workspace, rhqr_sketch_apply, rhqr_sketch_apply_workspace,
                rhqr_sketch_create, rhqr_sketch_destroy, rhqr_sketch_export, rhqr_sketch_shape, rhqr_workspace_size)
 
 TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}
@@ -49,6 +50,17 @@ class Sketch:
         G = torch.empty((self.k, self.n), dtype=TORCH_DTYPE[self.omega_dtype], device=device)
         rhqr_sketch_export(self.handle, None, None, G, self.n)
         return {"G": G}
+
+    def apply_rows(self, X_local: torch.Tensor, m: int, row0: int) -> torch.Tensor:
+        """One row shard's share Psi_m[:, row0:row0+rows] X_local of the sketch
+        (rhqr_sketch_apply_rows); the shards' results sum to apply(X, m)."""
+        rows, c = X_local.shape
+        ws_b = rhqr_sketch_apply_rows_workspace(self.handle, m, dtype_code(X_local), row0, rows, c)
+        ws = torch.empty(max(ws_b, 1), dtype=torch.uint8, device=X_local.device)
+        Z = colmajor(torch.zeros((self.k + m, c), dtype=torch.float64, device=X_local.device))
+        rhqr_sketch_apply_rows(self.handle, m, X_local, dtype_code(X_local), row0, rows, c, ld_of(X_local), Z, ld_of(Z),
+                               ws, ws_b)
+        return Z
 
     def apply(self, X: torch.Tensor, m: int) -> torch.Tensor:
         """Z = Psi_m X (Algorithm 1), X column-major n x c."""
