@@ -63,6 +63,7 @@ struct Params {
   float *part;  // [nch][k][c]
   const char *gt;  // operator tiles (256 x 64, 32 KiB each), gt_nkb per row of tiles
   int64_t gt_nkb;
+  const float *colscale;  // per column of X: exact power-of-two scale before the limb split, or NULL
   int *err;
   long long budget;
 };
@@ -226,6 +227,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const float4 f = src[32 * e4 + lane];
             v[4 * e4] = f.x, v[4 * e4 + 1] = f.y, v[4 * e4 + 2] = f.z, v[4 * e4 + 3] = f.w;
           }
+          if (P.colscale != nullptr) {
+#pragma unroll
+            for (int e4 = 0; e4 < 4; ++e4) {
+              const int col = col0 + 8 * g + 2 * e4 + (lane >> 4);
+              const float sc = col < P.c ? P.colscale[col] : 1.f;
+#pragma unroll
+              for (int e = 0; e < 4; ++e) v[4 * e4 + e] *= sc;
+            }
+          }
           if (top) {
 #pragma unroll
             for (int e4 = 0; e4 < 4; ++e4)
@@ -260,6 +270,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const float4 *src = reinterpret_cast<const float4 *>(xs + nn * BK + cidx * 8);
         float4 a = src[0], b = src[1];
         float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        if (P.colscale != nullptr) {
+          const float sc = col0 + nn < P.c ? P.colscale[col0 + nn] : 1.f;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] *= sc;
+        }
         if (top) {
 #pragma unroll
           for (int e = 0; e < 8; ++e)
@@ -296,6 +311,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const uint32_t run = tmem + lane_base + (uint32_t)(RUN_COL + h * 128);
     const int cc = col0 + qd * 32 + lane;
     const bool own_col = qd * 32 + lane < P.Nt && cc < P.c;
+    const float unscale = (own_col && P.colscale != nullptr) ? 1.f / P.colscale[cc] : 1.f;  // a power of two
     const int row0 = mt * BM + h * 128;
     bool ok = true;
     for (int d = 0; d < drains; ++d) {
@@ -320,7 +336,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           if (own_col) {
             for (int j = 0; j < 32; ++j) {
               const int row = row0 + c0 + j;
-              if (row < P.k) P.part[((int64_t)ch * P.k + row) * P.c + cc] = __uint_as_float(r[j]);
+              if (row < P.k) P.part[((int64_t)ch * P.k + row) * P.c + cc] = __uint_as_float(r[j]) * unscale;
             }
           }
         } else {
@@ -364,6 +380,40 @@ __global__ void reduce_part_kernel(const float *part, int32_t nch, int32_t k, in
   for (int ch = 0; ch < nch; ++ch) acc += (double)part[(int64_t)ch * k * c + idx];
   int64_t r = idx / c, col = idx - r * c;
   Z[col * ldz + ztop + r] = failed ? __longlong_as_double(0x7ff8000000000000LL) : acc * scale;
+}
+
+// fp16 limbs: f16 keeps 5 exponent bits, so the lower limbs of data of small
+// magnitude would fall below its normal range (2^-14) and lose digits.  Each
+// column is scaled by the power of two that brings its largest magnitude into
+// [2^14, 2^15) before the split (exact), and the partial sums are scaled back.
+// The column maxima take one read of X spread over the whole GPU.
+// column max |x| over row chunks (grid: columns x chunks), as float bits
+// (non-negative floats order like their bit patterns)
+__global__ void colmax_kernel(const float *X, int64_t ldx, int64_t n, unsigned int *mx) {
+  __shared__ unsigned int bmax;
+  if (threadIdx.x == 0) bmax = 0u;
+  __syncthreads();
+  const float *x = X + (int64_t)blockIdx.x * ldx;
+  const int64_t chunk = (n + gridDim.y - 1) / gridDim.y;
+  const int64_t r0 = (int64_t)blockIdx.y * chunk, r1 = min(n, r0 + chunk);
+  unsigned int local = 0u;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) local = max(local, __float_as_uint(fabsf(x[i])));
+  atomicMax(&bmax, local);
+  __syncthreads();
+  if (threadIdx.x == 0) atomicMax(mx + blockIdx.x, bmax);
+}
+
+__global__ void colscale_kernel(const unsigned int *mx, int32_t c, float *scale) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= c) return;
+  const float v = __uint_as_float(mx[j]);
+  float sc = 1.f;
+  if (v > 0.f && isfinite(v)) {
+    int e = 0;
+    frexpf(v, &e);  // v in [2^(e-1), 2^e)
+    sc = ldexpf(1.f, max(-120, min(120, 15 - e)));
+  }
+  scale[j] = sc;
 }
 
 __global__ void copy_top_f32_kernel(const float *X, int64_t ldx, int32_t m, int32_t c, double *Z, int64_t ldz) {
@@ -443,7 +493,8 @@ bool sketch_tc_supported(const SketchView &s, int64_t n, int32_t m, int32_t c) {
 
 size_t sketch_tc_workspace_bytes(const SketchView &s, int64_t n, int32_t m, int32_t c) {
   if (c < 1 || n <= m) return 0;
-  return align_up((size_t)tc_nchunks(s, n, m, c, nullptr) * s.k * c * sizeof(float), 256) + 256;
+  return align_up((size_t)tc_nchunks(s, n, m, c, nullptr) * s.k * c * sizeof(float), 256) + 256 +
+         align_up((size_t)c * sizeof(float), 256);
 }
 
 rhqr_status sketch_apply_tc(const SketchView &s, int32_t m, const float *X, int64_t n, int32_t c, int64_t ldx,
@@ -455,10 +506,22 @@ rhqr_status sketch_apply_tc(const SketchView &s, int32_t m, const float *X, int6
   int64_t kchunk = 0;
   const int64_t nch = tc_nchunks(s, n, m, c, &kchunk);
   size_t part_bytes = align_up((size_t)nch * s.k * c * sizeof(float), 256);
-  if (ws_bytes < part_bytes + 256) return RHQR_ENOMEM;
+  const size_t scale_bytes = align_up((size_t)c * sizeof(float), 256);
+  if (ws_bytes < part_bytes + 256 + scale_bytes) return RHQR_ENOMEM;
   float *part = (float *)ws;
   int *err = (int *)((char *)ws + part_bytes);
+  float *colscale = (float *)((char *)ws + part_bytes + 256);
   RHQR_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+  const bool scaled = s.omega_dtype == RHQR_F16;
+  if (scaled) {
+    unsigned int *mx = reinterpret_cast<unsigned int *>(colscale);  // maxima first, then the scales in place
+    RHQR_CUDA_TRY(cudaMemsetAsync(mx, 0, (size_t)c * sizeof(unsigned int), st));
+    const unsigned chunks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(152 * 8, c), ceil_div(n, 4096)));
+    tc::colmax_kernel<<<dim3((unsigned)c, chunks), 256, 0, st>>>(X, ldx, n, mx);
+    RHQR_LAUNCH_CHECK();
+    tc::colscale_kernel<<<(unsigned)ceil_div(c, 256), 256, 0, st>>>(mx, c, colscale);
+    RHQR_LAUNCH_CHECK();
+  }
 
   const int32_t Np = (int32_t)ceil_div(c, 16) * 16;
   const int32_t Nt = std::min<int32_t>(tc::NT, Np);
@@ -489,6 +552,7 @@ rhqr_status sketch_apply_tc(const SketchView &s, int32_t m, const float *X, int6
   P.part = part;
   P.gt = (const char *)s.Gt;
   P.gt_nkb = s.gt_nkb;
+  P.colscale = scaled ? colscale : nullptr;
   P.err = err;
   P.budget = budget > 0 ? budget : kDefaultWaitBudget;
   const size_t stage_bytes = tc::A_BYTES + tc::X_BYTES + (limbs <= 2 ? 0 : (size_t)limbs * tc::B_BYTES);
