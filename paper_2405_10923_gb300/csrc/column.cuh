@@ -114,6 +114,126 @@ __global__ void __launch_bounds__(256) left_refresh_kernel(ColArgs a0) {
   }
 }
 
+// Vector form of the refresh for 16-byte aligned columns (ldw, ldu multiples
+// of 16 bytes, aligned bases): each thread takes V = 16 / sizeof(T)
+// consecutive rows with one 16-byte load per column; rows past the last full
+// vector go through the scalar loop of the first thread of the grid.
+template <class T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int V = 4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int V = 2;
+};
+
+template <class T>
+__global__ void __launch_bounds__(256) left_refresh_vec_kernel(ColArgs a0) {
+  using VT = typename Vec16<T>::type;
+  constexpr int V = Vec16<T>::V;
+  const ColArgs a = batch_args<T>(a0);
+  __shared__ T c_s[1024];
+  const int j = a.j, lo = a.lo, nc = j - lo;
+  for (int l = threadIdx.x; l < nc; l += blockDim.x) c_s[l] = (T)a.c[l];
+  const T inv_g = (j - 1 >= lo) ? (T)(1.0 / a.gamma[j - 1]) : T(1);
+  __syncthreads();
+  const T *W = (const T *)a.W;
+  T *U = (T *)a.U;
+  const int64_t ldu = a.ldu;
+  const int nfull = nc > 0 ? nc - 1 : 0;
+  const int64_t nvec = a.n / V;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nvec + (a.n % V != 0);
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = q * V;
+    T w[V];
+    if (q < nvec) {
+      T p[4][V];
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int e = 0; e < V; ++e) p[t][e] = T(0);
+      const T *up = U + (int64_t)lo * ldu + i0;
+      int l = 0;
+      for (; l + 4 <= nfull; l += 4) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const VT u = *reinterpret_cast<const VT *>(up + t * ldu);
+          const T *ue = reinterpret_cast<const T *>(&u);
+#pragma unroll
+          for (int e = 0; e < V; ++e) p[t][e] += ue[e] * c_s[l + t];
+        }
+        up += 4 * ldu;
+      }
+      for (; l < nfull; ++l, up += ldu) {
+        const VT u = *reinterpret_cast<const VT *>(up);
+        const T *ue = reinterpret_cast<const T *>(&u);
+#pragma unroll
+        for (int e = 0; e < V; ++e) p[l & 3][e] += ue[e] * c_s[l];
+      }
+      const VT wv = *reinterpret_cast<const VT *>(W + (int64_t)j * a.ldw + i0);
+      const T *we = reinterpret_cast<const T *>(&wv);
+#pragma unroll
+      for (int e = 0; e < V; ++e) w[e] = we[e] - ((p[0][e] + p[1][e]) + (p[2][e] + p[3][e]));
+      if (j - 1 >= lo) {
+        T *ul = U + (int64_t)(j - 1) * ldu + i0;
+        VT uv = *reinterpret_cast<const VT *>(ul);
+        T *ue = reinterpret_cast<T *>(&uv);
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          const int64_t i = i0 + e;
+          const T u = (i < j - 1) ? T(0) : ((i == j - 1 && a.unit) ? T(1) : ue[e] * inv_g);
+          ue[e] = u;
+          w[e] -= u * c_s[nc - 1];
+        }
+        *reinterpret_cast<VT *>(ul) = uv;
+      }
+      VT out;
+      T *oe = reinterpret_cast<T *>(&out);
+#pragma unroll
+      for (int e = 0; e < V; ++e) oe[e] = w[e];
+      *reinterpret_cast<VT *>(U + (int64_t)j * ldu + i0) = out;
+#pragma unroll
+      for (int e = 0; e < V; ++e)
+        if (i0 + e < a.m) a.y[i0 + e] = (double)w[e];
+    } else {
+      // the last n % V rows, one at a time (the same arithmetic as refresh_row)
+      for (int64_t i = i0; i < a.n; ++i) {
+        T ps[4] = {T(0), T(0), T(0), T(0)};
+        for (int l = 0; l < nfull; ++l) ps[l & 3] += U[(int64_t)(lo + l) * ldu + i] * c_s[l];
+        T wi = W[(int64_t)j * a.ldw + i] - ((ps[0] + ps[1]) + (ps[2] + ps[3]));
+        if (j - 1 >= lo) {
+          T *ul = U + (int64_t)(j - 1) * ldu + i;
+          const T u = (i < j - 1) ? T(0) : ((i == j - 1 && a.unit) ? T(1) : *ul * inv_g);
+          *ul = u;
+          wi -= u * c_s[nc - 1];
+        }
+        U[(int64_t)j * ldu + i] = wi;
+        if (i < a.m) a.y[i] = (double)wi;
+      }
+    }
+  }
+}
+
+// The refresh of column j (nprob problems of a batch) with the whole GPU: the
+// vector kernel when every column start is 16-byte aligned, else the scalar one.
+template <class T>
+static rhqr_status launch_refresh(const ColArgs &ca, unsigned nprob, cudaStream_t st) {
+  constexpr int V = Vec16<T>::V;
+  const bool aligned = ca.ldw % V == 0 && ca.ldu % V == 0 && ((uintptr_t)ca.W % 16) == 0 &&
+                       ((uintptr_t)ca.U % 16) == 0 && (nprob == 1 || (ca.bt.W % V == 0 && ca.bt.U % V == 0));
+  const int64_t units = aligned ? ceil_div(ca.n, V) : ca.n;
+  const dim3 g((unsigned)std::min<int64_t>(ceil_div(units, 256), std::max<int64_t>(1, 152 * 8 / (int64_t)nprob)),
+               nprob);
+  if (aligned) left_refresh_vec_kernel<T><<<g, 256, 0, st>>>(ca);
+  else left_refresh_kernel<T><<<g, 256, 0, st>>>(ca);
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
+}
+
 // SRHT: block j1 owns rows [j1 N2, (j1+1) N2); refresh (or read the refreshed
 // column), signs, FWHT, keep samples
 template <class T, bool REFRESHED>

@@ -216,8 +216,7 @@ static rhqr_status left_typed(const SketchView &s, const T *W, int64_t n, int32_
     ca.j = j;
     if (s.kind == RHQR_SKETCH_SRHT) {
       // refresh with the whole GPU, then sign / transform / sample the refreshed column
-      left_refresh_kernel<T><<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8), 256, 0, st>>>(ca);
-      RHQR_LAUNCH_CHECK();
+      RHQR_TRY(launch_refresh<T>(ca, 1, st));
       RHQR_TRY(column_srht<T>(ca, s, (T *)stage, 1, st));
       left_srht_combine_kernel<T><<<(unsigned)ceil_div(s.k, 8), 256, 0, st>>>(
           (const T *)stage, s.N1, s.d2, s.sample_i1, s.sample_slot, s.k, m, scale, y);
@@ -398,7 +397,6 @@ static rhqr_status block_typed(const SketchView &s, const T *W, int64_t n, int32
   RHQR_CUDA_TRY(cudaMemcpy2DAsync(U, (size_t)ldu * sizeof(T), W, (size_t)ldw * sizeof(T), (size_t)n * sizeof(T),
                                   (size_t)m, cudaMemcpyDeviceToDevice, st));
   const double scale = 1.0 / sqrt((double)s.k);
-  const unsigned upd_grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
   ColArgs ca{U, ldu, U, ldu, n, m, 0, cbuf, gam, y, scaling == 0 ? 1 : 0, 0, m};
   for (int32_t c0 = 0; c0 < m; c0 += bs) {
     const int32_t c1 = std::min(m, c0 + bs), nb = c1 - c0;
@@ -427,8 +425,7 @@ static rhqr_status block_typed(const SketchView &s, const T *W, int64_t n, int32
       }
       ca.j = j;
       if (s.kind == RHQR_SKETCH_SRHT) {
-        left_refresh_kernel<T><<<upd_grid, 256, 0, st>>>(ca);
-        RHQR_LAUNCH_CHECK();
+        RHQR_TRY(launch_refresh<T>(ca, 1, st));
         RHQR_TRY(column_srht<T>(ca, s, (T *)stage, 1, st));
         left_srht_combine_kernel<T><<<(unsigned)ceil_div(s.k, 8), 256, 0, st>>>(
             (const T *)stage, s.N1, s.d2, s.sample_i1, s.sample_slot, s.k, m, scale, y);
@@ -614,9 +611,7 @@ static rhqr_status arnoldi_reflect(ArnoldiState &a, const T *w, double *h, rhqr_
              Batch{a.n, a.ldu * M, M, p, a.stage_elems}};
   const double scale = 1.0 / sqrt((double)a.view.k);
   if (a.view.kind == RHQR_SKETCH_SRHT) {
-    dim3 gr((unsigned)std::min<int64_t>(ceil_div(a.n, 256), std::max<int64_t>(1, 152 * 8 / B)), (unsigned)B);
-    left_refresh_kernel<T><<<gr, 256, 0, st>>>(ca);
-    RHQR_LAUNCH_CHECK();
+    RHQR_TRY(launch_refresh<T>(ca, (unsigned)B, st));
     RHQR_TRY(column_srht<T>(ca, a.view, (T *)a.stage, (unsigned)B, st));
     left_srht_combine_kernel<T><<<dim3((unsigned)ceil_div(a.view.k, 8), (unsigned)B), 256, 0, st>>>(
         (const T *)a.stage, a.view.N1, a.view.d2, a.view.sample_i1, a.view.sample_slot, a.view.k, M, scale, a.y,

@@ -338,7 +338,6 @@ static rhqr_status trim_typed(const SketchView &s, const T *W, int64_t n, int32_
   RHQR_LAUNCH_CHECK();
 
   const double scale = 1.0 / sqrt((double)k);
-  const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
   // the column kernels copy the refreshed column's top m rows to x and sketch all rows
   ColArgs ca{W, ldw, U, ldu, n, m, 0, cbuf, gam, x, scaling == 0 ? 1 : 0, 0, 0};
   for (int32_t j = 0; j < m; ++j) {
@@ -348,8 +347,7 @@ static rhqr_status trim_typed(const SketchView &s, const T *W, int64_t n, int32_
     }
     ca.j = j;
     if (s.kind == RHQR_SKETCH_SRHT) {
-      left_refresh_kernel<T><<<grid, 256, 0, st>>>(ca);
-      RHQR_LAUNCH_CHECK();
+      RHQR_TRY(launch_refresh<T>(ca, 1, st));
       RHQR_TRY(column_srht<T>(ca, s, (T *)stage, 1, st));
       left_srht_combine_kernel<T><<<(unsigned)ceil_div(k, 8), 256, 0, st>>>(
           (const T *)stage, s.N1, s.d2, s.sample_i1, s.sample_slot, k, 0, scale, zw);
