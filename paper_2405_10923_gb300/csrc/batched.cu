@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "fwht.cuh"
 #include "sketch.cuh"
 
 namespace rhqr {
@@ -100,6 +101,42 @@ __global__ void __launch_bounds__(1024) b_srht_a_kernel(const BatchProb *P, int 
     }
     T *Y = reinterpret_cast<T *>(ws + B.off_Y) + ((int64_t)col * B.N1 + j1) * B.d2;
     for (int s = threadIdx.x; s < B.d2; s += blockDim.x) Y[s] = v[B.i2[s]];
+  }
+}
+
+// The same for batches whose problems all have 8192-entry segments (every
+// N >= 8192): 512 threads, the register / shuffle transform of fwht.cuh.
+template <class T>
+__global__ void __launch_bounds__(512) b_srht_a_fwht_kernel(const BatchProb *P, int count, int pass, char *ws,
+                                                            int64_t items) {
+  constexpr int NT = 512;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *buf = reinterpret_cast<T *>(smem_raw);
+  const int t = threadIdx.x;
+  for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+    const int pi = find_prob_a(P, count, item);
+    const BatchProb &B = P[pi];
+    const int64_t local = item - B.a_begin;
+    const int col = (int)(local / B.N1), j1 = (int)(local % B.N1);
+    const T *X = pass == 0 ? (const T *)B.W : (const T *)B.Q;
+    const int64_t ldx = pass == 0 ? B.ldx : B.ldq;
+    const T *x = X + (int64_t)col * ldx;
+    const int64_t row0 = (int64_t)j1 * 8192;
+    T v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int64_t i = row0 + r * NT + t;
+      T val = T(0);
+      if (i >= B.m && i < B.n) {
+        val = x[i];
+        if ((B.signs[i >> 5] >> (i & 31)) & 1u) val = -val;
+      }
+      v[r] = val;
+    }
+    __syncthreads();  // the previous item's samples are read before buf is rewritten
+    fwht_segment<T, 13>(v, buf);
+    T *Y = reinterpret_cast<T *>(ws + B.off_Y) + ((int64_t)col * B.N1 + j1) * B.d2;
+    for (int s2 = t; s2 < B.d2; s2 += NT) Y[s2] = buf[B.i2[s2]];
   }
 }
 
@@ -334,7 +371,7 @@ struct rhqr_batch_s {
   BatchProb *dev;
   size_t ws_bytes;
   int64_t itemsA, itemsB, itemsS[3];
-  int32_t maxN2, maxmp;
+  int32_t maxN2, minN2, maxmp;
   // launch shapes (set by the tuner): stage-A threads, solve rows per block,
   // solve grid cap (0 = one block per row block)
   int32_t a_threads, solve_rb, solve_cap;
@@ -360,6 +397,15 @@ static rhqr_status batch_set_smem(size_t smemA, size_t smemS32) {
 
 template <class T>
 static rhqr_status batch_stage_a(const rhqr_batch_s *b, char *w, int pass, int threads, cudaStream_t st) {
+  if (b->minN2 == 8192 && b->maxN2 == 8192) {
+    const size_t smem = 8192 * sizeof(T);
+    RHQR_CUDA_TRY(cudaFuncSetAttribute(b_srht_a_fwht_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    const unsigned g = (unsigned)std::min<int64_t>(b->itemsA, 152 * 4);
+    b_srht_a_fwht_kernel<T><<<g, 512, smem, st>>>(b->dev, b->count, pass, w, b->itemsA);
+    RHQR_LAUNCH_CHECK();
+    return RHQR_OK;
+  }
   const unsigned g = (unsigned)std::min<int64_t>(b->itemsA, 152 * 2048 / threads * 2);
   b_srht_a_kernel<T><<<g, threads, (size_t)b->maxN2 * sizeof(T), st>>>(b->dev, b->count, pass, w, b->itemsA);
   RHQR_LAUNCH_CHECK();
@@ -494,6 +540,7 @@ rhqr_status rhqr_batch_create(int32_t count, const rhqr_sketch *s, const void *c
   };
   int64_t a = 0, bb = 0, sblk[3] = {0, 0, 0};
   b->maxN2 = 1;
+  b->minN2 = 1 << 30;
   b->maxmp = 32;
   const size_t es = dtype_size(wt);
   for (int i = 0; i < count; ++i) {
@@ -546,6 +593,7 @@ rhqr_status rhqr_batch_create(int32_t count, const rhqr_sketch *s, const void *c
       sblk[r] += ceil_div(n[i], 32 << r);
     }
     b->maxN2 = std::max(b->maxN2, v.N2);
+    b->minN2 = std::min(b->minN2, v.N2);
     b->maxmp = std::max(b->maxmp, P.mp);
   }
   b->itemsA = a;
