@@ -235,6 +235,25 @@ size_t sketch_apply_workspace_bytes(const SketchView &s, int32_t m, int32_t xt, 
   return align_up((size_t)nch * s.k * c * sizeof(double), 256) + 256;
 }
 
+// Stage B for many columns at once: one thread per (sampled row, column),
+// the N1 segment values summed in order (enough threads without splitting a row).
+template <class T>
+__global__ void srht_stage_b_rows_kernel(const T *Y, int32_t N1, int32_t d2, const int32_t *sample_i1,
+                                         const int32_t *sample_slot, int32_t k, int32_t m, double scale, double *Z,
+                                         int64_t ldz, int32_t seg0) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int col = blockIdx.y;
+  if (r >= k) return;
+  const int i1 = sample_i1[r], slot = sample_slot[r];
+  const T *y = Y + (int64_t)col * N1 * d2 + slot;
+  double acc = 0.0;
+  for (int j1 = 0; j1 < N1; ++j1) {
+    const double t = to_f64<T>(y[(int64_t)j1 * d2]);
+    acc += (__popc(i1 & (seg0 + j1)) & 1) ? -t : t;
+  }
+  Z[(int64_t)col * ldz + m + r] = acc * scale;
+}
+
 // Stage A over the segments seg0 .. seg0 + nseg - 1 of the window's rows,
 // stage B summing them with the global segment signs: Z[m + r, col] for the
 // rows in the window (the whole column, or a shard's share of the sum).
@@ -257,9 +276,15 @@ static rhqr_status srht_apply(const SketchView &s, int32_t m, const TX *X, int64
       RHQR_LAUNCH_CHECK();
     }
   }
-  dim3 gb((unsigned)ceil_div(s.k, 8), c);
-  srht_stage_b_kernel<TX><<<gb, 256, 0, st>>>(Y, nseg, s.d2, s.sample_i1, s.sample_slot, s.k, m,
-                                               1.0 / sqrt((double)s.k), Z, ldz, win.seg0);
+  if (c >= 16) {  // enough (row, column) pairs to fill the GPU with one thread each
+    dim3 gb((unsigned)ceil_div(s.k, 128), c);
+    srht_stage_b_rows_kernel<TX><<<gb, 128, 0, st>>>(Y, nseg, s.d2, s.sample_i1, s.sample_slot, s.k, m,
+                                                      1.0 / sqrt((double)s.k), Z, ldz, win.seg0);
+  } else {  // few columns: a warp per sampled row
+    dim3 gb((unsigned)ceil_div(s.k, 8), c);
+    srht_stage_b_kernel<TX><<<gb, 256, 0, st>>>(Y, nseg, s.d2, s.sample_i1, s.sample_slot, s.k, m,
+                                                 1.0 / sqrt((double)s.k), Z, ldz, win.seg0);
+  }
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }
