@@ -303,6 +303,22 @@ def run_ours(a, rank: int, world: int, local_rank: int):
     e1.record()
     torch.cuda.synchronize()
     d2h_gbs = bytes_w / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    # both directions at once (W in on one stream, Q out on another): whether
+    # this host link carries them concurrently decides whether the pipeline's
+    # copy-in and copy-out can overlap each other
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    e0.record()
+    s_in.wait_event(e0)
+    s_out.wait_event(e0)
+    with torch.cuda.stream(s_in):
+        W.t().copy_(Wh.t(), non_blocking=True)
+    with torch.cuda.stream(s_out):
+        Qh[1].t().copy_(out["Q"].t(), non_blocking=True)
+    torch.cuda.current_stream().wait_stream(s_in)
+    torch.cuda.current_stream().wait_stream(s_out)
+    e1.record()
+    torch.cuda.synchronize()
+    both_gbs = 2.0 * bytes_w / (e0.elapsed_time(e1) * 1e-3) / 1e9
     e2e_steps = max(2, a.steps)
     torch.cuda.synchronize()
     barrier()
@@ -399,7 +415,8 @@ def run_ours(a, rank: int, world: int, local_rank: int):
         "e2e": {"value": replica_throughput(world, bytes_w, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": bytes_w,
                 "d2h_bytes_per_step": bytes_w + m * m * 8, "steps": e2e_steps, "ms_per_step": e2e_ms,
                 "path": "rhqr_pipeline (host W in, host Q and R out; copies overlap neighbouring steps)",
-                "link_h2d_gbs": h2d_gbs, "link_d2h_gbs": d2h_gbs, "q_equals_device_path": e2e_ok},
+                "link_h2d_gbs": h2d_gbs, "link_d2h_gbs": d2h_gbs, "link_both_directions_gbs": both_gbs,
+                "q_equals_device_path": e2e_ok},
         "gpu_launches": int(launches),
         "clocks": clk,
     }
