@@ -103,6 +103,7 @@ struct Params {
   int32_t m, nprod, split, bregion;  // nprod: 6, 3, or 0 = chosen from max |F|
   int32_t use_tma;                   // X staged by TMA (16-byte aligned X and ld), else column loads
   int32_t use_tma_y;                 // Q written by TMA stores from shared memory, else column stores
+  int32_t inplace;                   // Y == X: a tile is stored only after both CTAs have read it
   const double *Rinv;
   CtaPlan plan[2];
   rhqr_info *info;
@@ -173,9 +174,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   float *ybuf = xst + 2 * (XST_BYTES / 4);                     // 2 pieces of Q [col][row]
   float *dvec = ybuf + 2 * (YST_BYTES / 4);
   uint64_t *bars = reinterpret_cast<uint64_t *>(dvec + MAXM);
-  uint64_t *a_full = bars, *a_empty = bars + 2, *acc_full = bars + 4, *acc_empty = bars + 6;
-  uint64_t *x_full = bars + 8, *x_empty = bars + 10;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 12);
+  // accumulator barriers per buffer b and owned column chunk ci: [2 b + ci]
+  uint64_t *a_full = bars, *a_empty = bars + 2, *acc_full = bars + 4, *acc_empty = bars + 8;
+  uint64_t *x_full = bars + 12, *x_empty = bars + 14;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 17);
   volatile int *abort_s = reinterpret_cast<volatile int *>(tmem_slot + 1);
   int *err_s = reinterpret_cast<int *>(tmem_slot + 2);
   unsigned int *fmax_s = tmem_slot + 3;  // max |F| of this CTA's blocks (float bits, >= 0)
@@ -191,8 +193,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     for (int s = 0; s < 2; ++s) {
       tc::mbar_init(a_full + s, 4);
       tc::mbar_init(a_empty + s, 1);
-      tc::mbar_init(acc_full + s, 1);
-      tc::mbar_init(acc_empty + s, 4);
+      for (int ci = 0; ci < 2; ++ci) {
+        tc::mbar_init(acc_full + 2 * s + ci, 1);
+        tc::mbar_init(acc_empty + 2 * s + ci, 4);
+      }
       tc::mbar_init(x_full + s, 1);
       tc::mbar_init(x_empty + s, 4);
     }
@@ -288,7 +292,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t it = 0;
       for (int64_t t = t0; t < ntiles && ok; t += tstep, ++it) {
         const uint32_t b = it % nbuf, u = it / nbuf;
-        if (!tc::mbar_wait(acc_empty + b, (u & 1u) ^ 1u, P.budget, err_s, abort_s)) break;
+        // the first group writes every owned chunk: all of them drained
+        for (int ci = 0; ci < C.ncc && ok; ++ci)
+          ok = tc::mbar_wait(acc_empty + 2 * b + ci, (u & 1u) ^ 1u, P.budget, err_s, abort_s);
+        if (!ok) break;
         tc::fence_after();
         const uint32_t acc = tmem + (uint32_t)(ACC_COL0 + b * MAX_W);
         for (int kc = 0; kc < C.nk; ++kc, ++gch) {
@@ -308,9 +315,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           else if (G.diag) issue_group<4, false>(dcol, a_stage, dhi, blo, lstride, idesc, first);
           else issue_group<3, false>(dcol, a_stage, dhi, blo, lstride, idesc, first);
           tc::mma_commit(a_empty + s);
+          // one accumulator buffer (six products): an owned chunk is complete
+          // after its diagonal group, and the epilogue drains it while the later
+          // groups run; two buffers: the tile is handed over whole
+          if (nbuf == 1)
+            for (int ci = 0; ci < C.ncc; ++ci)
+              if (C.cc[ci] == kc) tc::mma_commit(acc_full + 2 * b + ci);
         }
         if (!ok) break;
-        tc::mma_commit(acc_full + b);
+        if (nbuf == 2) tc::mma_commit(acc_full + 2 * b);
       }
       tc::mma_quiesce(mma_done);  // no MMA in flight when tensor memory is released
     }
@@ -420,37 +433,50 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int r = qd * 32 + lane;
     const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
     uint32_t it = 0, piece = 0;
-    for (int64_t t = t0; t < ntiles; t += tstep, ++it) {
+    bool ok_all = true;
+    for (int64_t t = t0; t < ntiles && ok_all; t += tstep, ++it) {
       const uint32_t b = it % nbuf, u = it / nbuf;
-      bool okw = tc::warp_wait(acc_full + b, u & 1u, P.budget, err_s, abort_s);
-      // the four epilogue warps share named barriers: they stop together
-      if (P.use_tma_y) okw = tc::named_and(1, 128, okw);
-      if (!okw) break;
-      tc::fence_after();
-      if (P.split) {  // in place: the peer's loaders must be done with this tile
-        const uint32_t need = 128u * (uint32_t)(it + 1);
-        long long spins = 0;
-        bool ok = true;
-        while (tc::ld_acquire_cluster(peer_cnt) < need || tc::ld_acquire_cluster(peer_cnt + 1) < need) {
-          if (*abort_s) {
-            ok = false;
-            break;
-          }
-          if (++spins > P.budget) {
-            atomicExch(err_s, 1);
-            *abort_s = 1;
-            ok = false;
-            break;
-          }
-        }
-        ok = __all_sync(0xffffffffu, ok);
-        if (P.use_tma_y) ok = tc::named_and(1, 128, ok);
-        if (!ok) break;
-      }
       const int64_t row = t * TILE + r;
       const bool live = row < P.nrows;
       const bool issuer = qd == 0 && lane == 0;  // the epilogue thread that issues TMA stores
+      // owned chunks in the order the MMA thread completes them; each one's
+      // accumulator columns are released as soon as they have been read
       for (int ci = 0; ci < C.ncc; ++ci) {
+        // two accumulator buffers: one commit for the whole tile (the next
+        // tile's MMAs do not wait for this drain)
+        bool okw = true;
+        if (nbuf == 1 || ci == 0) okw = tc::mbar_wait(acc_full + 2 * b + (nbuf == 1 ? ci : 0), u & 1u, P.budget, err_s, abort_s);
+        okw = __all_sync(0xffffffffu, okw);
+        // the four epilogue warps share named barriers: they stop together
+        if (P.use_tma_y) okw = tc::named_and(1, 128, okw);
+        if (!okw) {
+          ok_all = false;
+          break;
+        }
+        tc::fence_after();
+        if (ci == 0 && P.split && P.inplace) {  // the peer's loaders must be done with this tile
+          const uint32_t need = 128u * (uint32_t)(it + 1);
+          long long spins = 0;
+          bool ok = true;
+          while (tc::ld_acquire_cluster(peer_cnt) < need || tc::ld_acquire_cluster(peer_cnt + 1) < need) {
+            if (*abort_s) {
+              ok = false;
+              break;
+            }
+            if (++spins > P.budget) {
+              atomicExch(err_s, 1);
+              *abort_s = 1;
+              ok = false;
+              break;
+            }
+          }
+          ok = __all_sync(0xffffffffu, ok);
+          if (P.use_tma_y) ok = tc::named_and(1, 128, ok);
+          if (!ok) {
+            ok_all = false;
+            break;
+          }
+        }
         if (P.use_tma_y) {
           // pieces of 32 (or a last 16) columns: TMEM -> shared memory -> one TMA store
           for (int c0 = 0; c0 < C.cc_w[ci]; c0 += 32, ++piece) {
@@ -461,14 +487,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             for (int h = 0; h < wc / 16; ++h) {
               const uint32_t col =
                   tmem + lane_base + (uint32_t)(ACC_COL0 + b * MAX_W + C.cc_acc[ci] + c0 + 16 * h);
-              uint32_t a[16], a2[16];
-              tc::tmem_ld16(col, a);
-              if (two) tc::tmem_ld16(col + (uint32_t)MAX_W, a2);
+              uint32_t a0[16], b0[16];
+              tc::tmem_ld16(col, a0);
+              if (two) tc::tmem_ld16(col + (uint32_t)MAX_W, b0);
               tc::tmem_wait_ld();
 #pragma unroll
               for (int j = 0; j < 16; ++j)
                 yb[(16 * h + j) * TILE + r] =
-                    two ? __uint_as_float(a[j]) + __uint_as_float(a2[j]) : __uint_as_float(a[j]);
+                    two ? __uint_as_float(a0[j]) + __uint_as_float(b0[j]) : __uint_as_float(a0[j]);
             }
             tc::fence_proxy_async();
             tc::named_sync(1, 128);
@@ -478,28 +504,28 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
               tc::bulk_commit();
             }
           }
-          continue;
-        }
-        for (int cb = 0; cb < C.cc_w[ci] / 16; ++cb) {
-          const uint32_t col = tmem + lane_base + (uint32_t)(ACC_COL0 + b * MAX_W + C.cc_acc[ci] + cb * 16);
-          uint32_t a[16], a2[16];
-          tc::tmem_ld16(col, a);
-          if (two) tc::tmem_ld16(col + (uint32_t)MAX_W, a2);
-          tc::tmem_wait_ld();
-          if (live) {
-            const int col0 = C.cc[ci] * 64 + cb * 16;
-            float *y = P.Y + (int64_t)col0 * P.ldy + row;
+        } else {
+          for (int cb = 0; cb < C.cc_w[ci] / 16; ++cb) {
+            const uint32_t col = tmem + lane_base + (uint32_t)(ACC_COL0 + b * MAX_W + C.cc_acc[ci] + cb * 16);
+            uint32_t a0[16], b0[16];
+            tc::tmem_ld16(col, a0);
+            if (two) tc::tmem_ld16(col + (uint32_t)MAX_W, b0);
+            tc::tmem_wait_ld();
+            if (live) {
+              const int col0 = C.cc[ci] * 64 + cb * 16;
+              float *y = P.Y + (int64_t)col0 * P.ldy + row;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const float v = two ? __uint_as_float(a[j]) + __uint_as_float(a2[j]) : __uint_as_float(a[j]);
-              if (col0 + j < m) y[(int64_t)j * P.ldy] = v;
+              for (int j = 0; j < 16; ++j) {
+                const float v = two ? __uint_as_float(a0[j]) + __uint_as_float(b0[j]) : __uint_as_float(a0[j]);
+                if (col0 + j < m) y[(int64_t)j * P.ldy] = v;
+              }
             }
           }
         }
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(acc_empty + 2 * b + ci);
       }
-      tc::fence_before();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(acc_empty + b);
     }
     if (P.use_tma_y && qd == 0 && lane == 0) tc::bulk_wait_all();  // stores complete before exit
   }
@@ -547,7 +573,7 @@ static bool make_plan(const int *own, int nown, int mp, CtaPlan &C) {
 }
 
 static size_t smem_bytes(int bregion) {
-  return 1024 + (size_t)bregion + 2 * XST_BYTES + 2 * YST_BYTES + MAXM * 4 + 17 * 8 + 64;
+  return 1024 + (size_t)bregion + 2 * XST_BYTES + 2 * YST_BYTES + MAXM * 4 + 21 * 8 + 64;
 }
 
 // Column chunks of the one or two CTAs per tile and the shared-memory size.
@@ -602,6 +628,7 @@ rhqr_status rows_solve_inv_tc(const float *X, int64_t ldx, int64_t nrows, int32_
   P.Rinv = Rinv;
   P.info = info;
   P.budget = budget;
+  P.inplace = X == Y ? 1 : 0;
   CUtensorMap mapX;
   std::memset(&mapX, 0, sizeof(mapX));
   P.use_tma = 0;
