@@ -487,6 +487,15 @@ rhqr_status rhqr_sketch_apply_noalloc(rhqr_sketch s, int32_t m, const void *X, i
  *   Q formation, 4 other small FP64 work, 5 left-looking column steps.
  */
 int64_t rhqr_launch_count(void);
+
+/*
+ * rhqr_last_cuda_error: the CUDA runtime error code (cudaError_t value) of the
+ * most recent call of this library that returned RHQR_ECUDA, 0 if none did;
+ * process-wide, not per thread.  rhqr_cuda_error_name: its name (a static
+ * string owned by the CUDA runtime, e.g. "cudaErrorInvalidClusterSize").
+ */
+int32_t rhqr_last_cuda_error(void);
+const char *rhqr_cuda_error_name(int32_t code);
 void rhqr_profile_enable(int32_t on);
 int32_t rhqr_profile_read(double *ms /* host, n */, int64_t *calls /* host, n */, int32_t n);
 

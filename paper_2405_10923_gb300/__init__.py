@@ -39,7 +39,10 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 class RHQRError(RuntimeError):
     def __init__(self, func: str, code: int):
         self.code = code
-        super().__init__(f"{func} failed: {STATUS.get(code, code)}")
+        msg = f"{func} failed: {STATUS.get(code, code)}"
+        if STATUS.get(code) == "RHQR_ECUDA":
+            msg += " ({1}, code {0})".format(*rhqr_last_cuda_error())
+        super().__init__(msg)
 
 
 class rhqr_opts(ctypes.Structure):
@@ -123,6 +126,8 @@ _SIGNATURES = {
     "rhqr_pipeline_wait": (_i32, [_p]),
     "rhqr_pipeline_destroy": (_i32, [_p]),
     "rhqr_launch_count": (_i64, []),
+    "rhqr_last_cuda_error": (_i32, []),
+    "rhqr_cuda_error_name": (ctypes.c_char_p, [_i32]),
     "rhqr_profile_enable": (None, [_i32]),
     "rhqr_profile_read": (_i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
 }
@@ -453,6 +458,12 @@ def rhqr_pipeline_destroy(p) -> None:
 
 def rhqr_launch_count() -> int:
     return load().rhqr_launch_count()
+
+
+def rhqr_last_cuda_error() -> tuple[int, str]:
+    """CUDA error code and name of the last call that returned RHQR_ECUDA (0 if none)."""
+    code = load().rhqr_last_cuda_error()
+    return code, load().rhqr_cuda_error_name(code).decode()
 
 
 def rhqr_profile_enable(on: bool) -> None:

@@ -10,11 +10,14 @@
 
 namespace rhqr {
 
-// Launch/runtime error -> RHQR_ECUDA (synchronous part of the contract).
+// Launch/runtime error -> RHQR_ECUDA (synchronous part of the contract); the
+// CUDA error code is kept for rhqr_last_cuda_error.
+void note_cuda_error(cudaError_t e);
 #define RHQR_CUDA_TRY(expr)                                    \
   do {                                                         \
     cudaError_t e_ = (expr);                                   \
     if (e_ != cudaSuccess) {                                   \
+      ::rhqr::note_cuda_error(e_);                             \
       (void)cudaGetLastError();                                \
       return RHQR_ECUDA;                                       \
     }                                                          \

@@ -20,6 +20,9 @@ static long long g_calls[PH_COUNT];
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+static std::atomic<int> g_last_cuda_error{0};
+void note_cuda_error(cudaError_t e) { g_last_cuda_error.store((int)e, std::memory_order_relaxed); }
+
 PhaseScope::PhaseScope(int ph, cudaStream_t s) : phase(ph), st(s), ev(nullptr) {
   if (!g_profile_on.load(std::memory_order_relaxed)) return;
   cudaEvent_t *e = new cudaEvent_t[2];
@@ -63,6 +66,10 @@ using namespace rhqr;
 extern "C" {
 
 int64_t rhqr_launch_count(void) { return g_launches.load(); }
+
+int32_t rhqr_last_cuda_error(void) { return g_last_cuda_error.load(); }
+
+const char *rhqr_cuda_error_name(int32_t code) { return cudaGetErrorName((cudaError_t)code); }
 
 void rhqr_profile_enable(int32_t on) {
   std::lock_guard<std::mutex> lk(g_mu);

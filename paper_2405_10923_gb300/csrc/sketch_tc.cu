@@ -93,6 +93,94 @@ struct Limb<__half> {
   }
 };
 
+// Converters, limbs written in place (L <= 2): one warp per group of 8 columns
+// (2 KiB of float32, 64 rows each).  Load e4 of lane l is float4 f = 32 e4 + l:
+// column f / 16, rows 4 (f % 16) .. + 3, so each 8-lane phase reads 128
+// contiguous bytes (no bank conflicts); the lane then writes its 4 rows of each
+// limb as 8 bytes of the swizzled atom row of that column.  Rows below m (the
+// exact top block) are zeroed.
+template <class TL, int L>
+__device__ __forceinline__ void convert_inplace(const float *xs, uint8_t *bst_in, const Params &P, int col0,
+                                                int64_t r0, int wg, int lane) {
+  const bool top = r0 < P.m;
+  for (int g = wg; g < P.Nt / 8; g += NUM_CONV_WARPS) {
+    const float4 *src = reinterpret_cast<const float4 *>(xs + 8 * g * BK);
+    float v[16];
+#pragma unroll
+    for (int e4 = 0; e4 < 4; ++e4) {
+      const float4 f = src[32 * e4 + lane];
+      v[4 * e4] = f.x, v[4 * e4 + 1] = f.y, v[4 * e4 + 2] = f.z, v[4 * e4 + 3] = f.w;
+    }
+    if (P.colscale != nullptr) {
+#pragma unroll
+      for (int e4 = 0; e4 < 4; ++e4) {
+        const int col = col0 + 8 * g + 2 * e4 + (lane >> 4);
+        const float sc = col < P.c ? P.colscale[col] : 1.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[4 * e4 + e] *= sc;
+      }
+    }
+    if (top) {
+#pragma unroll
+      for (int e4 = 0; e4 < 4; ++e4)
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (r0 + 4 * ((32 * e4 + lane) & 15) + e < P.m) v[4 * e4 + e] = 0.f;
+    }
+    __syncwarp();  // the whole group is read before its bytes are overwritten
+    uint8_t *atom = bst_in + g * 2048;
+#pragma unroll
+    for (int e4 = 0; e4 < 4; ++e4) {
+      const int f = 32 * e4 + lane, n = f >> 4, row = 4 * (f & 15);
+      const uint32_t off =
+          (uint32_t)n * 128u + ((((uint32_t)row >> 3) ^ (uint32_t)(n & 7)) << 4) + (uint32_t)((row & 7) * 2);
+      float *vv = v + 4 * e4;
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        float rr[4];
+        uint2 w;
+        w.x = Limb<TL>::pack(vv[0], vv[1], rr[0], rr[1]);
+        w.y = Limb<TL>::pack(vv[2], vv[3], rr[2], rr[3]);
+        *reinterpret_cast<uint2 *>(atom + l * 1024 + off) = w;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) vv[e] = rr[e];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Drainers, one drain: thread -> one column of X (tensor-memory lane), 128
+// accumulator columns (rows of G) starting at `fresh`; the running sums at
+// `run` take the fresh accumulator with round-to-nearest adds, and the last
+// drain writes them to the float32 partial of chunk `ch`.
+__device__ __forceinline__ void drain_once(uint32_t fresh, uint32_t run, bool first, bool last, bool own_col,
+                                           float unscale, int row0, int cc, int ch, const Params &P) {
+  for (int c0 = 0; c0 < 128; c0 += 32) {
+    uint32_t f[32], r[32];
+    tmem_ld32(fresh + c0, f);
+    if (!first) tmem_ld32(run + c0, r);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      float v = __uint_as_float(f[j]);
+      if (!first) v = __fadd_rn(__uint_as_float(r[j]), v);
+      r[j] = __float_as_uint(v);
+    }
+    if (last) {
+      if (own_col) {
+        for (int j = 0; j < 32; ++j) {
+          const int row = row0 + c0 + j;
+          if (row < P.k) P.part[((int64_t)ch * P.k + row) * P.c + cc] = __uint_as_float(r[j]) * unscale;
+        }
+      }
+    } else {
+      tmem_st32(run + c0, r);
+    }
+  }
+  tmem_wait_st();
+}
+
 template <class TL, int L>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     sketch_tc_kernel(const __grid_constant__ CUtensorMap tmapX, Params P) {
@@ -214,56 +302,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int64_t r0 = x_begin + (int64_t)i * BK;
       const bool top = r0 < P.m;  // rows below m are the exact top block: excluded
       if (INPLACE) {
-        // One warp per group of 8 columns (2 KiB of float32, 64 rows each).  Load
-        // e4 of lane l is float4 f = 32 e4 + l: column f / 16, rows 4 (f % 16) ..
-        // + 3, so each 8-lane phase reads 128 contiguous bytes (no bank
-        // conflicts); the lane then writes its 4 rows of each limb as 8 bytes of
-        // the swizzled atom row of that column.
-        for (int g = warp - CONV_WARP0; g < P.Nt / 8; g += NUM_CONV_WARPS) {
-          const float4 *src = reinterpret_cast<const float4 *>(xs + 8 * g * BK);
-          float v[16];
-#pragma unroll
-          for (int e4 = 0; e4 < 4; ++e4) {
-            const float4 f = src[32 * e4 + lane];
-            v[4 * e4] = f.x, v[4 * e4 + 1] = f.y, v[4 * e4 + 2] = f.z, v[4 * e4 + 3] = f.w;
-          }
-          if (P.colscale != nullptr) {
-#pragma unroll
-            for (int e4 = 0; e4 < 4; ++e4) {
-              const int col = col0 + 8 * g + 2 * e4 + (lane >> 4);
-              const float sc = col < P.c ? P.colscale[col] : 1.f;
-#pragma unroll
-              for (int e = 0; e < 4; ++e) v[4 * e4 + e] *= sc;
-            }
-          }
-          if (top) {
-#pragma unroll
-            for (int e4 = 0; e4 < 4; ++e4)
-#pragma unroll
-              for (int e = 0; e < 4; ++e)
-                if (r0 + 4 * ((32 * e4 + lane) & 15) + e < P.m) v[4 * e4 + e] = 0.f;
-          }
-          __syncwarp();  // the whole group is read before its bytes are overwritten
-          uint8_t *atom = bst_in + g * 2048;
-#pragma unroll
-          for (int e4 = 0; e4 < 4; ++e4) {
-            const int f = 32 * e4 + lane, n = f >> 4, row = 4 * (f & 15);
-            const uint32_t off = (uint32_t)n * 128u + ((((uint32_t)row >> 3) ^ (uint32_t)(n & 7)) << 4) +
-                                 (uint32_t)((row & 7) * 2);
-            float *vv = v + 4 * e4;
-#pragma unroll
-            for (int l = 0; l < L; ++l) {
-              float rr[4];
-              uint2 w;
-              w.x = Limb<TL>::pack(vv[0], vv[1], rr[0], rr[1]);
-              w.y = Limb<TL>::pack(vv[2], vv[3], rr[2], rr[3]);
-              *reinterpret_cast<uint2 *>(atom + l * 1024 + off) = w;
-#pragma unroll
-              for (int e = 0; e < 4; ++e) vv[e] = rr[e];
-            }
-          }
-          __syncwarp();
-        }
+        convert_inplace<TL, L>(xs, bst_in, P, col0, r0, warp - CONV_WARP0, lane);
       } else
       for (int q = ct; q < P.Nt * 8; q += NUM_CONV_WARPS * 32) {
         const int nn = q >> 3, cidx = q & 7;
@@ -320,30 +359,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         break;
       }
       fence_after();
-      const bool last = (d == drains - 1);
-      for (int c0 = 0; c0 < 128; c0 += 32) {
-        uint32_t f[32], r[32];
-        tmem_ld32(fresh + c0, f);
-        if (d > 0) tmem_ld32(run + c0, r);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          float v = __uint_as_float(f[j]);
-          if (d > 0) v = __fadd_rn(__uint_as_float(r[j]), v);
-          r[j] = __float_as_uint(v);
-        }
-        if (last) {
-          if (own_col) {
-            for (int j = 0; j < 32; ++j) {
-              const int row = row0 + c0 + j;
-              if (row < P.k) P.part[((int64_t)ch * P.k + row) * P.c + cc] = __uint_as_float(r[j]) * unscale;
-            }
-          }
-        } else {
-          tmem_st32(run + c0, r);
-        }
-      }
-      tmem_wait_st();
+      drain_once(fresh, run, d == 0, d == drains - 1, own_col, unscale, row0, cc, ch, P);
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(fresh_empty);
@@ -356,6 +372,203 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     fence_after();
     tmem_dealloc(tmem, 512);
   }
+}
+
+// The same sketch on CTA pairs (cta_group::2), for two column tiles of X
+// (128 < c <= 256) and L <= 2 limbs.  The pair (a cluster of 2 along x: rank
+// 0 and 1 = column tiles 0 and 1 of one G tile and K-chunk) issues one
+// M = 256, N = 256 MMA per 16 rows and limb: M covers the two CTAs' 128
+// columns of X each, and the G tile's 256 rows are split between them, rank r
+// holding rows 128 r .. 128 r + 127.  Each SM thus stages and reads half of G,
+// the operand that dominates the shared-memory reads of the single-CTA
+// kernel, while its tensor memory still receives all 256 rows of G for its
+// 128 columns.  Rank 0 issues the MMAs once both CTAs' converters have filled
+// a stage, and its commits arrive on both CTAs' barriers.  Converters and
+// drainers arrive on their own CTA's barriers only (an arrival with
+// cluster-scope release costs more than the conversion of a stage); in rank
+// 1, two lanes of the otherwise idle warp 1 wait for each completed stage and
+// each completed drain and forward it to rank 0 with one remote arrival.
+constexpr int G_HALF_BYTES = A_BYTES / 2;  // 128 rows of the G tile
+constexpr int PAIR_STAGES = 4;
+
+template <class TL, int L>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    sketch_tc_pair_kernel(const __grid_constant__ CUtensorMap tmapX, Params P) {
+  static_assert(L <= 2, "limbs are written in place");
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int S = PAIR_STAGES;
+  constexpr int stage_bytes = G_HALF_BYTES + X_BYTES;
+  uint64_t *bars = (uint64_t *)(smem + S * stage_bytes);
+  uint64_t *full_a = bars, *full_b = bars + S, *empty = bars + 2 * S;
+  uint64_t *fresh_full = bars + 3 * S, *fresh_empty = bars + 3 * S + 1, *mma_done = bars + 3 * S + 2;
+  uint32_t *tmem_slot = (uint32_t *)(bars + 3 * S + 3);
+  volatile int *abort_s = (volatile int *)(bars + 3 * S + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();  // = blockIdx.x: column tile
+  const bool leader = rank == 0;
+  const int mt = blockIdx.y, ch = blockIdx.z;
+  const int col0 = (int)rank * P.Nt;
+  const int64_t x_begin = (int64_t)P.m64 + (int64_t)ch * P.kchunk;
+  const int64_t x_end = min(P.n, x_begin + P.kchunk);
+  const int steps = (int)((x_end - x_begin + BK - 1) / BK);
+  const int per_drain = P.kdrain / BK;
+  const int drains = (steps + per_drain - 1) / per_drain;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full_a + s, 1);
+      mbar_init(full_b + s, leader ? NUM_CONV_WARPS + 1 : NUM_CONV_WARPS);  // rank 0: + rank 1's forward
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(fresh_full, 1);
+    mbar_init(fresh_empty, leader ? NUM_DRAIN_WARPS + 1 : NUM_DRAIN_WARPS);
+    mbar_init(mma_done, 1);
+    *abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc2(tmem_slot, 512);
+    tmem_relinquish2();
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  cluster_sync();  // both CTAs' barriers are initialised before any remote arrival
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer (both CTAs): this CTA's half of the G tile and its X tile
+      int issued = 0;
+      for (int i = 0; i < steps; ++i) {
+        const int s = i % S;
+        const uint32_t ph = (uint32_t)(i / S) & 1u;
+        if (!mbar_wait(empty + s, ph ^ 1u, P.budget, P.err, abort_s)) break;
+        uint8_t *st = smem + s * stage_bytes;
+        mbar_expect_tx(full_a + s, (uint32_t)(G_HALF_BYTES + P.xbytes));
+        const int xr = (int)(x_begin + (int64_t)i * BK);
+        bulk_load(st, P.gt + ((int64_t)mt * P.gt_nkb + xr / BK) * A_BYTES + (int64_t)rank * G_HALF_BYTES,
+                  G_HALF_BYTES, full_a + s);
+        tma_load_2d(st + G_HALF_BYTES, &tmapX, full_a + s, xr, col0);
+        ++issued;
+      }
+      for (int i = max(0, issued - S); i < issued; ++i) drain_wait(full_a + (i % S), (uint32_t)(i / S) & 1u);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && leader) {
+      const uint32_t idesc = idesc_f16(256, BM, Limb<TL>::fmt);  // M: the pair's 256 columns of X, N: 256 rows of G
+      int i = 0;
+      for (int d = 0; d < drains && i < steps; ++d) {
+        if (d > 0 && !mbar_wait_cluster(fresh_empty, (uint32_t)(d - 1) & 1u, P.budget, P.err, abort_s)) break;
+        fence_after();
+        bool ok = true;
+        for (int j = 0; j < per_drain && i < steps; ++j, ++i) {
+          const int s = i % S;
+          const uint32_t ph = (uint32_t)(i / S) & 1u;
+          if (!mbar_wait(full_a + s, ph, P.budget, P.err, abort_s) ||
+              !mbar_wait_cluster(full_b + s, ph, P.budget, P.err, abort_s)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t st_base = smem_u32(smem + s * stage_bytes);
+          const uint64_t gd0 = sw128_desc(st_base);                       // this CTA's 128 rows of G
+          const uint64_t xd0 = sw128_desc(st_base + G_HALF_BYTES, 2048);  // limbs, written in place
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+#pragma unroll
+            for (int l = 0; l < L; ++l)
+              mma_ss2(tmem, xd0 + (uint64_t)((l * 1024 + kk * 32) >> 4), gd0 + (uint64_t)((kk * 32) >> 4), idesc,
+                      (uint32_t)(j != 0 || kk != 0 || l != 0));
+          mma_commit2(empty + s);
+        }
+        mma_commit2(fresh_full);
+        if (!ok) break;
+      }
+      mma_commit2(mma_done);  // no MMA in flight when tensor memory is released (both CTAs)
+    } else if (!leader && lane == 0) {
+      // forward each stage completed by this CTA's converters to rank 0
+      const uint32_t full_b0 = map_to_rank(full_b, 0u);
+      for (int i = 0; i < steps; ++i) {
+        const int s = i % S;
+        if (!mbar_wait(full_b + s, (uint32_t)(i / S) & 1u, P.budget, P.err, abort_s)) break;
+        mbar_arrive_cluster(full_b0 + (uint32_t)(s * 8));
+      }
+    } else if (!leader && lane == 1) {
+      // forward each drain completed by this CTA's drainers to rank 0
+      const uint32_t fresh_empty0 = map_to_rank(fresh_empty, 0u);
+      for (int d = 0; d < drains; ++d) {
+        if (!mbar_wait(fresh_empty, (uint32_t)d & 1u, P.budget, P.err, abort_s)) break;
+        mbar_arrive_cluster(fresh_empty0);
+      }
+    }
+    __syncwarp();
+  } else if (warp >= CONV_WARP0 && warp < CONV_WARP0 + NUM_CONV_WARPS) {
+    for (int i = 0; i < steps; ++i) {
+      const int s = i % S;
+      const uint32_t ph = (uint32_t)(i / S) & 1u;
+      if (!warp_wait(full_a + s, ph, P.budget, P.err, abort_s)) break;
+      uint8_t *st = smem + s * stage_bytes;
+      const int64_t r0 = x_begin + (int64_t)i * BK;
+      convert_inplace<TL, L>(reinterpret_cast<const float *>(st + G_HALF_BYTES), st + G_HALF_BYTES, P, col0, r0,
+                             warp - CONV_WARP0, lane);
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(full_b + s);
+    }
+  } else if (warp >= DRAIN_WARP0) {
+    const int dw = warp - DRAIN_WARP0;
+    const int h = dw >> 2, qd = warp & 3;
+    const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
+    const uint32_t fresh = tmem + lane_base + (uint32_t)(h * 128);
+    const uint32_t run = tmem + lane_base + (uint32_t)(RUN_COL + h * 128);
+    const int cc = col0 + qd * 32 + lane;
+    const bool own_col = qd * 32 + lane < P.Nt && cc < P.c;
+    const float unscale = (own_col && P.colscale != nullptr) ? 1.f / P.colscale[cc] : 1.f;  // a power of two
+    const int row0 = mt * BM + h * 128;
+    for (int d = 0; d < drains; ++d) {
+      if (!warp_wait(fresh_full, (uint32_t)d & 1u, P.budget, P.err, abort_s)) break;
+      fence_after();
+      drain_once(fresh, run, d == 0, d == drains - 1, own_col, unscale, row0, cc, ch, P);
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(fresh_empty);
+    }
+  }
+  // every MMA of the pair has completed (rank 0's last commit reaches both
+  // CTAs) before either CTA releases tensor memory
+  if (warp == 1 && lane == 0) drain_wait(mma_done, 0u);
+  fence_before();
+  __syncthreads();
+  cluster_sync();  // no remote arrival or MMA access after this point
+  if (warp == 1) {
+    fence_after();
+    tmem_dealloc2(tmem, 512);
+  }
+}
+
+template <class TL, int L>
+static rhqr_status launch_sketch_pair(dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap &mapX,
+                                      const Params &P) {
+  RHQR_CUDA_TRY(
+      cudaFuncSetAttribute(sketch_tc_pair_kernel<TL, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;  // the pair: the two column tiles (x) of one G tile and K-chunk
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(2, grid.x, grid.z);
+  cfg.blockDim = dim3(NUM_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  RHQR_CUDA_TRY(cudaLaunchKernelEx(&cfg, sketch_tc_pair_kernel<TL, L>, mapX, P));
+  RHQR_LAUNCH_CHECK();
+  return RHQR_OK;
 }
 
 template <class TL, int L>
@@ -558,7 +771,18 @@ rhqr_status sketch_apply_tc(const SketchView &s, int32_t m, const float *X, int6
   const size_t stage_bytes = tc::A_BYTES + tc::X_BYTES + (limbs <= 2 ? 0 : (size_t)limbs * tc::B_BYTES);
   size_t smem = 1024 + (size_t)P.stages * stage_bytes + 256;
   dim3 grid((unsigned)ceil_div(s.k, tc::BM), (unsigned)ceil_div(Np, Nt), (unsigned)nch);
-  if (s.omega_dtype == RHQR_BF16) {
+  if (grid.y == 2 && limbs <= 2) {
+    // two column tiles: CTA pairs sharing each G tile (cta_group::2)
+    P.stages = tc::PAIR_STAGES;
+    const size_t smem2 = 1024 + (size_t)tc::PAIR_STAGES * (tc::G_HALF_BYTES + tc::X_BYTES) + 256;
+    if (s.omega_dtype == RHQR_BF16) {
+      if (limbs == 1) RHQR_TRY((tc::launch_sketch_pair<__nv_bfloat16, 1>(grid, smem2, st, mapX, P)));
+      else RHQR_TRY((tc::launch_sketch_pair<__nv_bfloat16, 2>(grid, smem2, st, mapX, P)));
+    } else {
+      if (limbs == 1) RHQR_TRY((tc::launch_sketch_pair<__half, 1>(grid, smem2, st, mapX, P)));
+      else RHQR_TRY((tc::launch_sketch_pair<__half, 2>(grid, smem2, st, mapX, P)));
+    }
+  } else if (s.omega_dtype == RHQR_BF16) {
     switch (limbs) {
       case 1: RHQR_TRY((tc::launch_sketch<__nv_bfloat16, 1>(grid, smem, st, mapX, P))); break;
       case 2: RHQR_TRY((tc::launch_sketch<__nv_bfloat16, 2>(grid, smem, st, mapX, P))); break;

@@ -143,6 +143,74 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                : "memory");
 }
 
+// ---- CTA pairs (cta_group::2): one MMA spans the tensor cores of two SMs ----
+// Every tcgen05 instruction of a kernel that uses these takes .cta_group::2:
+// one warp of each CTA of the pair allocates and frees tensor memory
+// collectively; the even CTA issues the MMAs; A (M = 256) is split by rows
+// and B by its N rows between the two shared memories (the same offsets in
+// both), and each CTA's tensor memory holds its 128 rows of D.  The pair lies
+// along x of the cluster.
+__device__ __forceinline__ void tmem_alloc2(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish2() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc2(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_ss2(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive on the mbarrier at `bar`'s offset in both CTAs of the pair once every
+// MMA issued so far by this thread has completed.
+__device__ __forceinline__ void mma_commit2(uint64_t *bar) {
+  const uint16_t mask = 3;
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+// Arrive (release at cluster scope) on an mbarrier of another CTA of the
+// cluster; `cluster_addr` from map_to_rank.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+// try_wait with acquire at cluster scope: pairs with arrivals made from the
+// peer CTA, whose earlier writes then become visible here.
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity, long long budget, int *err,
+                                                  volatile int *abort_s) {
+  long long it = 0;
+  while (!mbar_try_wait_cluster(bar, parity)) {
+    if (*abort_s) return false;
+    if (++it > budget) {
+      atomicExch(err, 1);
+      *abort_s = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
 // Polls granted to the waits of a block that is already stopping (copies and
 // MMAs it issued before the stop): these complete on their own, so the bound
 // only guards against a fault, independently of the caller's wait budget.

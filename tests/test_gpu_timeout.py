@@ -21,12 +21,13 @@ ETIMEOUT = 6
 
 
 @pytest.mark.parametrize("solve", [0, 1])
-@pytest.mark.parametrize("kind", ["gaussian_bf16", "srht"])
-def test_tiny_wait_budget_times_out_and_recovers(gpu_lib, kind, solve):
+@pytest.mark.parametrize("kind,m", [("gaussian_bf16", 128), ("srht", 128), ("gaussian_bf16", 256)])
+def test_tiny_wait_budget_times_out_and_recovers(gpu_lib, kind, m, solve):
+    """m = 256 sketches two column tiles of X on CTA pairs (cta_group::2)."""
     import paper_2405_10923_gb300 as rh
     from paper_2405_10923_gb300 import torch_api as ta
 
-    n, m, k = 1 << 18, 128, 512
+    n, k = 1 << 18, 512
     W = rh.colmajor(torch.tensor(ri.gaussian(n, m, 50), dtype=torch.float32, device="cuda"))
     if kind == "srht":
         sk = ta.Sketch(n, k, gpu_lib.SRHT, 51)
