@@ -143,6 +143,14 @@ rhqr_status rhqr_pipeline_create(rhqr_sketch s, int32_t wt, int64_t n, int32_t m
   return RHQR_OK;
 }
 
+// Column-major block copy (rows x cols, element size es): one contiguous copy
+// when both leading dimensions equal the column length, else a pitched copy.
+static cudaError_t copy_cols(void *dst, int64_t dld, const void *src, int64_t sld, int64_t rows, int64_t cols,
+                             size_t es, cudaMemcpyKind kind, cudaStream_t st) {
+  if (dld == rows && sld == rows) return cudaMemcpyAsync(dst, src, (size_t)rows * (size_t)cols * es, kind, st);
+  return cudaMemcpy2DAsync(dst, (size_t)dld * es, src, (size_t)sld * es, (size_t)rows * es, (size_t)cols, kind, st);
+}
+
 rhqr_status rhqr_pipeline_submit(rhqr_pipeline p, const void *W, int64_t ldw, void *Q, int64_t ldq, double *R,
                                  double *S, int64_t lds, double *T, rhqr_info *info) {
   if (p == nullptr || W == nullptr || Q == nullptr || R == nullptr) return RHQR_EINVAL;
@@ -154,8 +162,7 @@ rhqr_status rhqr_pipeline_submit(rhqr_pipeline p, const void *W, int64_t ldw, vo
 
   // W in: the slot's previous factorisation must have finished reading W
   RHQR_CUDA_TRY(cudaStreamWaitEvent(p->s_in, sl.comp_done, 0));
-  RHQR_CUDA_TRY(cudaMemcpy2DAsync(sl.W, (size_t)ld * es, W, (size_t)ldw * es, (size_t)n * es, (size_t)m,
-                                  cudaMemcpyHostToDevice, p->s_in));
+  RHQR_CUDA_TRY(copy_cols(sl.W, ld, W, ldw, n, m, es, cudaMemcpyHostToDevice, p->s_in));
   RHQR_CUDA_TRY(cudaEventRecord(sl.in_done, p->s_in));
 
   // factorisation: after W arrived and after the previous outputs left
@@ -167,8 +174,7 @@ rhqr_status rhqr_pipeline_submit(rhqr_pipeline p, const void *W, int64_t ldw, vo
 
   // outputs out
   RHQR_CUDA_TRY(cudaStreamWaitEvent(p->s_out, sl.comp_done, 0));
-  RHQR_CUDA_TRY(cudaMemcpy2DAsync(Q, (size_t)ldq * es, sl.Q, (size_t)ld * es, (size_t)n * es, (size_t)m,
-                                  cudaMemcpyDeviceToHost, p->s_out));
+  RHQR_CUDA_TRY(copy_cols(Q, ldq, sl.Q, ld, n, m, es, cudaMemcpyDeviceToHost, p->s_out));
   RHQR_CUDA_TRY(cudaMemcpyAsync(R, sl.R, sizeof(double) * (size_t)m * m, cudaMemcpyDeviceToHost, p->s_out));
   if (S != nullptr)
     RHQR_CUDA_TRY(cudaMemcpy2DAsync(S, (size_t)lds * 8, sl.S, (size_t)pk * 8, (size_t)pk * 8, (size_t)m,
