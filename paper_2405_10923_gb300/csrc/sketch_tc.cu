@@ -153,14 +153,22 @@ __device__ __forceinline__ void convert_inplace(const float *xs, uint8_t *bst_in
 // Drainers, one drain: thread -> one column of X (tensor-memory lane), 128
 // accumulator columns (rows of G) starting at `fresh`; the running sums at
 // `run` take the fresh accumulator with round-to-nearest adds, and the last
-// drain writes them to the float32 partial of chunk `ch`.
+// drain writes them to the float32 partial of chunk `ch`.  The warp arrives on
+// `release` (the MMAs may overwrite the fresh accumulator) as soon as its last
+// load of it has completed, before the last adds and stores of the running sum.
 __device__ __forceinline__ void drain_once(uint32_t fresh, uint32_t run, bool first, bool last, bool own_col,
-                                           float unscale, int row0, int cc, int ch, const Params &P) {
+                                           float unscale, int row0, int cc, int ch, const Params &P,
+                                           uint64_t *release) {
   for (int c0 = 0; c0 < 128; c0 += 32) {
     uint32_t f[32], r[32];
     tmem_ld32(fresh + c0, f);
     if (!first) tmem_ld32(run + c0, r);
     tmem_wait_ld();
+    if (c0 == 96) {
+      fence_before();
+      __syncwarp();
+      if ((threadIdx.x & 31) == 0) mbar_arrive(release);
+    }
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       float v = __uint_as_float(f[j]);
@@ -359,10 +367,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         break;
       }
       fence_after();
-      drain_once(fresh, run, d == 0, d == drains - 1, own_col, unscale, row0, cc, ch, P);
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(fresh_empty);
+      drain_once(fresh, run, d == 0, d == drains - 1, own_col, unscale, row0, cc, ch, P, fresh_empty);
     }
     (void)ok;
   }
@@ -531,10 +536,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     for (int d = 0; d < drains; ++d) {
       if (!warp_wait(fresh_full, (uint32_t)d & 1u, P.budget, P.err, abort_s)) break;
       fence_after();
-      drain_once(fresh, run, d == 0, d == drains - 1, own_col, unscale, row0, cc, ch, P);
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(fresh_empty);
+      drain_once(fresh, run, d == 0, d == drains - 1, own_col, unscale, row0, cc, ch, P, fresh_empty);
     }
   }
   // every MMA of the pair has completed (rank 0's last commit reaches both
