@@ -5,9 +5,15 @@
 // beta = 1 + |z_jj| / rho, r_jj = -sigma rho).
 //
 // Panels of 32 columns.  A panel is factored by one cluster of CTAs that hold
-// its rows in shared memory; each column costs two cluster barriers, and the
+// its rows in shared memory; each column costs one cluster barrier, and the
 // partial sums of the CTAs are pushed into each other's shared memory and
-// added in a fixed order, so the result does not depend on timing.  The
+// added in a fixed order, so the result does not depend on timing.  The one
+// reduction per column takes the dots of the unscaled column z_j with every
+// panel column (its own: ||z_{j:}||^2) and, with row j of the panel pushed by
+// its owner, yields rho and every product the column needs: with
+// v_j(i) = rdiv z_j(i) below the diagonal and v_j(j) = vjj,
+//   v_j . y = vjj y(j) + rdiv (z_j . y - z_jj y(j))   (rows >= j)
+// for y = z_c (c > j) and y = v_k (k < j).  The
 // panel's reflectors are then applied to the trailing columns in compact form,
 // Z_t <- (I - V T^t V^t) Z_t, one CTA per trailing column.  T (upper
 // triangular, T_jj = beta_j) is never formed: T^{-1} = diag(1/beta) +
@@ -54,44 +60,67 @@ __global__ void __launch_bounds__(PT) hqr_panel_kernel(Args a) {
   const int nloc = (int)clamp64(p - row0, 0, per);
   const int ps = per | 1;  // odd column stride: lanes reading one row of 32 columns hit distinct banks
   double *pan = sm;                      // [NB][ps]: column c, local row i
-  double *part = sm + NB * ps;           // [MAXCS][NB + 1]: partial sums pushed by every CTA
-  double *gram = part + MAXCS * (NB + 1);  // [NB][NB]: gram[k * NB + l] = v_k . v_l (k < l), whole cluster
-  double *wsh = gram + NB * NB;          // [NB]
-  double *zsh = wsh + NB;                // [1]: z_jj pushed by its owner
-  double *red = zsh + 2;                 // [PT / 32][32]: per-warp partial dots
+  // part and zrow are double-buffered by column parity: a CTA pushes column
+  // j + 1's values while a slower peer may still be summing column j's (one
+  // cluster barrier per column), and it cannot reach column j + 2's push
+  // before that peer has passed column j + 1's barrier.
+  double *part0 = sm + NB * ps;           // [2][MAXCS][NB + 1]: partial sums pushed by every CTA
+  double *gram = part0 + 2 * MAXCS * (NB + 1);  // [NB][NB]: gram[k * NB + l] = v_k . v_l (k < l), whole cluster
+  double *wsh = gram + NB * NB;          // [NB]: beta (v_j . z_c)
+  double *zrow0 = wsh + NB;              // [2][NB]: row j of the panel, pushed by its owner
+  double *dsum = zrow0 + 2 * NB;         // [NB]: z_j . (column c), rows >= j, whole cluster
+  double *red = dsum + NB;               // [PT / 32][32]: per-warp partial dots
   for (int e = tid; e < nbp * per; e += PT) {
     const int c = e / per, i = e % per;
     pan[c * ps + i] = i < nloc ? a.A[(int64_t)(j0 + c) * p + row0 + i] : 0.0;
   }
   __syncthreads();
+  tc::cluster_sync();  // every CTA of the cluster runs before any pushes into its shared memory
   for (int jc = 0; jc < nbp; ++jc) {
     const int64_t j = (int64_t)j0 + jc;
     const int lo = (int)clamp64(j - row0, 0, nloc);  // first own row >= j
-    // ---- ||z_{j:}||^2: one warp's partial sum over this CTA's rows, pushed
-    //      (with z_jj from its owner) into every CTA of the cluster, added there
-    //      in rank order.  FP64 instructions are scarce on this GPU: the scalar
-    //      work of the column is done once, by thread 0.
     const uint32_t owner = (uint32_t)(jc / per);
-    if (warp == 0) {
-      double ss = 0.0;
-      for (int i = lo + lane; i < nloc; i += 32) ss += pan[jc * ps + i] * pan[jc * ps + i];
-      ss = warp_sum(ss);
-      if (lane < (int)cs) {
-        tc::st_cluster_f64(tc::map_to_rank(part + rank * (NB + 1), (uint32_t)lane), ss);
-        if (rank == owner) tc::st_cluster_f64(tc::map_to_rank(zsh, (uint32_t)lane), pan[jc * ps + (jc - (int)owner * per)]);
+    double *part = part0 + (jc & 1) * MAXCS * (NB + 1);
+    double *zrow = zrow0 + (jc & 1) * NB;
+    // ---- partial dots z_j . (column c) over this CTA's rows >= j, lane =
+    //      column (c = jc gives ||z_{j:}||^2), warp = every 8th own row: no
+    //      butterfly reductions (FP64 instructions are the scarce resource); the
+    //      8 warp partials of a column are added by a fixed tree and pushed to
+    //      every CTA, with row j of the panel from its owner.
+    {
+      double d = 0.0;
+      if (lane < nbp)
+        for (int i = lo + warp; i < nloc; i += PT / 32) d += pan[jc * ps + i] * pan[lane * ps + i];
+      red[warp * 32 + lane] = d;
+    }
+    __syncthreads();
+    if (warp == 0 && lane < nbp) {
+      const double *rw = red + lane;
+      const double d = ((rw[0] + rw[32]) + (rw[64] + rw[96])) + ((rw[128] + rw[160]) + (rw[192] + rw[224]));
+      const double zr = rank == owner ? pan[lane * ps + (jc - (int)owner * per)] : 0.0;
+      for (uint32_t r = 0; r < cs; ++r) {
+        tc::st_cluster_f64(tc::map_to_rank(part + rank * (NB + 1) + lane, r), d);
+        if (rank == owner) tc::st_cluster_f64(tc::map_to_rank(zrow + lane, r), zr);
       }
     }
     tc::cluster_sync();
-    double tot = 0.0;
-    if (warp == 0) {
-      // partials of the CTAs added by a fixed lane tree (lane r holds rank r's)
-      tot = lane < (int)cs ? part[lane * (NB + 1)] : 0.0;
-      tot = warp_sum(tot);
+    // sums over ranks, lane = column, by a fixed tree over the 16 (or fewer) ranks
+    if (warp == 0 && lane < nbp) {
+      double v[MAXCS];
+#pragma unroll
+      for (int r = 0; r < MAXCS; ++r) v[r] = r < (int)cs ? part[r * (NB + 1) + lane] : 0.0;
+#pragma unroll
+      for (int h = MAXCS / 2; h > 0; h >>= 1)
+#pragma unroll
+        for (int r = 0; r < h; ++r) v[r] = v[2 * r] + v[2 * r + 1];
+      dsum[lane] = v[0];
     }
+    __syncthreads();
     if (tid == 0) {
       // one reciprocal square root and one division per column (FP64 square
       // roots and divisions are long dependent sequences on this GPU)
-      const double zjj = *zsh;
+      const double tot = dsum[jc];
+      const double zjj = zrow[jc];
       const bool zero = tot == 0.0;
       const double rinv = rsqrt(tot);  // 1 / rho
       const double rho = tot * rinv;
@@ -127,44 +156,16 @@ __global__ void __launch_bounds__(PT) hqr_panel_kernel(Args a) {
       return;
     }
     const double beta = sh[0], rdiv = sh[1], vjj = sh[2];
+    // w_c = beta (v_j . z_c) for c > j; column j of the panel's V^t V for k < j
+    if (warp == 0 && lane < nbp && lane != jc) {
+      const double zjj = zrow[jc], y = zrow[lane];
+      const double vy = vjj * y + rdiv * (dsum[lane] - zjj * y);
+      if (lane > jc) wsh[lane] = beta * vy;
+      else gram[lane * NB + jc] = vy;
+    }
     for (int i = lo + tid; i < nloc; i += PT) {
       const int64_t gi = row0 + i;
       pan[jc * ps + i] = gi == j ? vjj : pan[jc * ps + i] * rdiv;
-    }
-    __syncthreads();
-    // ---- v . z_c for the panel columns c > j (then z_c -= beta v (v . z_c)),
-    //      and v . v_k for the reflectors k < j already formed: column j of the
-    //      panel's V^t V, from which T is built at the end (no second pass over
-    //      the rows).  Rows below j only: v_k and v vanish above their diagonals.
-    //      Lane = column, warp = every 8th own row: no butterfly reductions (FP64
-    //      instructions are the scarce resource); the 8 warp partials of a
-    //      column are added by a fixed tree and pushed to every CTA.
-    {
-      const bool col = lane < nbp && lane != jc;
-      double d = 0.0;
-      if (col)
-        for (int i = lo + warp; i < nloc; i += PT / 32) d += pan[jc * ps + i] * pan[lane * ps + i];
-      red[warp * 32 + lane] = d;
-    }
-    __syncthreads();
-    if (warp == 0 && lane < nbp && lane != jc) {
-      const double *rw = red + lane;
-      const double d = ((rw[0] + rw[32]) + (rw[64] + rw[96])) + ((rw[128] + rw[160]) + (rw[192] + rw[224]));
-      for (uint32_t r = 0; r < cs; ++r) tc::st_cluster_f64(tc::map_to_rank(part + rank * (NB + 1) + 1 + lane, r), d);
-    }
-    tc::cluster_sync();
-    // sums over ranks, lane = column, by a fixed tree over the 16 (or fewer)
-    // ranks; w_c = beta * sum for c > j, gram[k][j] = sum for k < j
-    if (warp == 0 && lane < nbp && lane != jc) {
-      double v[MAXCS];
-#pragma unroll
-      for (int r = 0; r < MAXCS; ++r) v[r] = r < (int)cs ? part[r * (NB + 1) + 1 + lane] : 0.0;
-#pragma unroll
-      for (int h = MAXCS / 2; h > 0; h >>= 1)
-#pragma unroll
-        for (int r = 0; r < h; ++r) v[r] = v[2 * r] + v[2 * r + 1];
-      if (lane > jc) wsh[lane] = beta * v[0];
-      else gram[lane * NB + jc] = v[0];
     }
     __syncthreads();
     for (int e = tid; e < (nbp - jc - 1) * (nloc - lo); e += PT) {
@@ -272,7 +273,7 @@ __global__ void hqr_r_kernel(const double *A, int64_t p, int32_t m, const double
 }
 
 static size_t panel_smem(int per) {
-  return sizeof(double) * ((size_t)NB * (per | 1) + (size_t)MAXCS * (NB + 1) + (size_t)NB * NB + NB + 2 + (size_t)PT);
+  return sizeof(double) * ((size_t)NB * (per | 1) + 2 * (size_t)MAXCS * (NB + 1) + (size_t)NB * NB + 4 * NB + (size_t)PT);
 }
 
 // Largest cluster (16, 8 or 4 CTAs) that fits the first panel of p rows.
