@@ -78,6 +78,7 @@ __device__ __forceinline__ T refresh_row(const ColArgs &a, int64_t i, const doub
 // top rows of the sketch.
 template <class T>
 __global__ void __launch_bounds__(256) left_refresh_kernel(ColArgs a0) {
+  pdl_wait();  // the refresh's coefficients come from the previous kernel
   const ColArgs a = batch_args<T>(a0);
   __shared__ T c_s[1024];  // coefficients, converted once
   const int j = a.j, lo = a.lo, nc = j - lo;
@@ -133,6 +134,7 @@ struct Vec16<double> {
 
 template <class T>
 __global__ void __launch_bounds__(256) left_refresh_vec_kernel(ColArgs a0) {
+  pdl_wait();  // the refresh's coefficients come from the previous kernel
   using VT = typename Vec16<T>::type;
   constexpr int V = Vec16<T>::V;
   const ColArgs a = batch_args<T>(a0);
@@ -228,8 +230,8 @@ static rhqr_status launch_refresh(const ColArgs &ca, unsigned nprob, cudaStream_
   const int64_t units = aligned ? ceil_div(ca.n, V) : ca.n;
   const dim3 g((unsigned)std::min<int64_t>(ceil_div(units, 256), std::max<int64_t>(1, 152 * 8 / (int64_t)nprob)),
                nprob);
-  if (aligned) left_refresh_vec_kernel<T><<<g, 256, 0, st>>>(ca);
-  else left_refresh_kernel<T><<<g, 256, 0, st>>>(ca);
+  if (aligned) RHQR_CUDA_TRY(launch_pdl(left_refresh_vec_kernel<T>, g, dim3(256), 0, st, ca));
+  else RHQR_CUDA_TRY(launch_pdl(left_refresh_kernel<T>, g, dim3(256), 0, st, ca));
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }
@@ -239,6 +241,8 @@ static rhqr_status launch_refresh(const ColArgs &ca, unsigned nprob, cudaStream_
 template <class T, bool REFRESHED>
 __global__ void left_column_srht_kernel(ColArgs a0, const uint32_t *sign_bits, int32_t N2, const int32_t *i2_list,
                                         int32_t d2, T *Ystage) {
+  pdl_wait();
+  pdl_release();
   const ColArgs a = batch_args<T>(a0);
   Ystage += (int64_t)blockIdx.y * a0.bt.stage;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -286,6 +290,8 @@ template <class T, int LOGN2>
 __global__ void __launch_bounds__(1 << (LOGN2 - 4)) column_srht_fwht_kernel(ColArgs a0, const uint32_t *sign_bits,
                                                                             const int32_t *i2_list, int32_t d2,
                                                                             T *Ystage) {
+  pdl_wait();
+  pdl_release();
   constexpr int N2 = 1 << LOGN2, NT = N2 / 16;
   const ColArgs a = batch_args<T>(a0);
   Ystage += (int64_t)blockIdx.y * a0.bt.stage;
@@ -317,8 +323,8 @@ static rhqr_status launch_column_fwht(const ColArgs &ca, const SketchView &v, T 
   if (smem > 48 * 1024)
     RHQR_CUDA_TRY(cudaFuncSetAttribute(column_srht_fwht_kernel<T, LOGN2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
-  column_srht_fwht_kernel<T, LOGN2><<<dim3((unsigned)v.N1, nprob), 1 << (LOGN2 - 4), smem, st>>>(
-      ca, v.sign_bits, v.i2_list, v.d2, stage);
+  RHQR_CUDA_TRY(launch_pdl(column_srht_fwht_kernel<T, LOGN2>, dim3((unsigned)v.N1, nprob), dim3(1 << (LOGN2 - 4)),
+                           smem, st, ca, v.sign_bits, v.i2_list, v.d2, stage));
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }
@@ -337,8 +343,8 @@ static rhqr_status column_srht(const ColArgs &ca, const SketchView &v, T *stage,
     default: break;
   }
   const size_t smem = (size_t)v.N2 * sizeof(T);
-  left_column_srht_kernel<T, true><<<dim3((unsigned)v.N1, nprob), 512, smem, st>>>(ca, v.sign_bits, v.N2, v.i2_list,
-                                                                                  v.d2, stage);
+  RHQR_CUDA_TRY(launch_pdl(left_column_srht_kernel<T, true>, dim3((unsigned)v.N1, nprob), dim3(512), smem, st, ca,
+                           v.sign_bits, v.N2, v.i2_list, v.d2, stage));
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }
@@ -351,6 +357,8 @@ template <class T>
 __global__ void left_srht_combine_kernel(const T *Ystage, int32_t N1, int32_t d2, const int32_t *sample_i1,
                                          const int32_t *sample_slot, int32_t k, int32_t m, double scale, double *y,
                                          int64_t bs_stage = 0, int64_t bs_y = 0) {
+  pdl_wait();
+  pdl_release();
   Ystage += (int64_t)blockIdx.y * bs_stage;
   y += (int64_t)blockIdx.y * bs_y;
   const int lane = threadIdx.x & 31;
@@ -371,6 +379,7 @@ constexpr int LG_RB = 256;
 template <class T, class TG>
 __global__ void __launch_bounds__(LG_RB) left_column_gauss_kernel(ColArgs a0, const TG *G, int64_t ldg, int32_t k,
                                                                   double *part) {
+  pdl_wait();
   const ColArgs a = batch_args<T>(a0);
   part += (int64_t)blockIdx.y * a0.bt.stage;
   __shared__ double w_s[LG_RB];
@@ -400,6 +409,8 @@ __global__ void __launch_bounds__(LG_RB) left_column_gauss_kernel(ColArgs a0, co
 
 static __global__ void left_gauss_reduce_kernel(const double *part, int32_t nb, int32_t k, int32_t m, double scale,
                                                 double *y, int64_t bs_stage = 0, int64_t bs_y = 0) {
+  pdl_wait();
+  pdl_release();
   part += (int64_t)blockIdx.y * bs_stage;
   y += (int64_t)blockIdx.y * bs_y;
   int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -413,6 +424,7 @@ static __global__ void left_gauss_reduce_kernel(const double *part, int32_t nb, 
 template <class T>
 __global__ void left_scale_last_kernel(T *U, int64_t ldu, int64_t n, int32_t j, const double *gamma, int32_t unit,
                                        int64_t bs_U = 0, int64_t bs_vec = 0) {
+  pdl_wait();
   U += (int64_t)blockIdx.y * bs_U;
   gamma += (int64_t)blockIdx.y * bs_vec;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

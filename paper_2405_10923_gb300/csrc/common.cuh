@@ -6,6 +6,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/rhqr.h"
 
 namespace rhqr {
@@ -51,6 +53,31 @@ struct PhaseScope {
 // Polls of a device-side wait before it gives up with RHQR_ETIMEOUT, unless
 // the caller sets rhqr_opts.wait_budget.
 constexpr long long kDefaultWaitBudget = 20000000LL;
+
+// Programmatic dependent launch (PDL).  A kernel launched with launch_pdl may
+// be scheduled before the previous kernel of its stream has finished; it must
+// call pdl_wait() before it touches anything that kernel writes (the wait
+// returns at once for a kernel launched without PDL).  pdl_release() lets the
+// next PDL kernel of the stream be scheduled now; its pdl_wait() still waits
+// for this kernel to complete and its writes to be visible.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 inline size_t dtype_size(int32_t t) {
   switch (t) {

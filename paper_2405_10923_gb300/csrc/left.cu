@@ -28,6 +28,8 @@ namespace rhqr {
 __global__ void left_dots_kernel(const double *S, int64_t lds, int64_t p, int32_t j, int32_t nd, const double *z,
                                  int32_t nv, double *d, double *v, int32_t lo, int64_t bs_S = 0, int64_t bs_z = 0,
                                  int64_t bs_vec = 0) {
+  pdl_wait();
+  pdl_release();
   __shared__ double red[32];
   S += (int64_t)blockIdx.z * bs_S;  // problem blockIdx.z of a batch
   z += (int64_t)blockIdx.z * bs_z;
@@ -56,6 +58,8 @@ __global__ void left_dots_kernel(const double *S, int64_t lds, int64_t p, int32_
 __global__ void left_tcol_coef_kernel(double *T, int32_t m, int32_t j, const double *beta, const double *d,
                                       const double *v, int32_t nc, double *c, int32_t lo, int64_t bs_T = 0,
                                       int64_t bs_vec = 0) {
+  pdl_wait();
+  pdl_release();
   T += (int64_t)blockIdx.x * bs_T;  // problem blockIdx.x of a batch (one block each)
   beta += (int64_t)blockIdx.x * bs_vec;
   d += (int64_t)blockIdx.x * bs_vec;
@@ -103,6 +107,8 @@ template <class T>
 __global__ void left_rhvector_kernel(const double *y, int64_t p, int32_t m, int32_t j, int32_t scaling, double *S,
                                      int64_t lds, double *R, double *beta, double *gamma_out, T *U, int64_t ldu,
                                      rhqr_info *info, int *stop, RhvBatch bb = RhvBatch{}) {
+  pdl_wait();
+  pdl_release();
   __shared__ double red[32];
   {
     const int64_t b = blockIdx.x;
@@ -207,10 +213,15 @@ static rhqr_status left_typed(const SketchView &s, const T *W, int64_t n, int32_
   for (int j = 0; j < m; ++j) {
     if (j >= 1) {
       // d_l = s_l . s_{j-1} (l < j-1) finishes column j-1 of T; v_l = s_l . z_j (l < j)
+      // the chain of each column is launched with PDL (launch_pdl): each kernel
+      // is scheduled while its predecessor runs and waits for it on the device
       dim3 g((unsigned)j, 2);
-      left_dots_kernel<<<g, 256, 0, st>>>(S, lds, p, j - 1, j - 1, Zraw + (int64_t)j * p, j, dbuf, vbuf, 0);
+      RHQR_CUDA_TRY(launch_pdl(left_dots_kernel, g, dim3(256), 0, st, (const double *)S, lds, p, j - 1, j - 1,
+                               (const double *)(Zraw + (int64_t)j * p), j, dbuf, vbuf, 0, (int64_t)0, (int64_t)0,
+                               (int64_t)0));
       RHQR_LAUNCH_CHECK();
-      left_tcol_coef_kernel<<<1, 1024, 0, st>>>(Tm, m, j - 1, beta, dbuf, vbuf, j, cbuf, 0);
+      RHQR_CUDA_TRY(launch_pdl(left_tcol_coef_kernel, dim3(1), dim3(1024), 0, st, Tm, m, j - 1, (const double *)beta,
+                               (const double *)dbuf, (const double *)vbuf, j, cbuf, 0, (int64_t)0, (int64_t)0));
       RHQR_LAUNCH_CHECK();
     }
     ca.j = j;
@@ -218,8 +229,9 @@ static rhqr_status left_typed(const SketchView &s, const T *W, int64_t n, int32_
       // refresh with the whole GPU, then sign / transform / sample the refreshed column
       RHQR_TRY(launch_refresh<T>(ca, 1, st));
       RHQR_TRY(column_srht<T>(ca, s, (T *)stage, 1, st));
-      left_srht_combine_kernel<T><<<(unsigned)ceil_div(s.k, 8), 256, 0, st>>>(
-          (const T *)stage, s.N1, s.d2, s.sample_i1, s.sample_slot, s.k, m, scale, y);
+      RHQR_CUDA_TRY(launch_pdl(left_srht_combine_kernel<T>, dim3((unsigned)ceil_div(s.k, 8)), dim3(256), 0, st,
+                               (const T *)stage, s.N1, s.d2, s.sample_i1, s.sample_slot, s.k, m, scale, y,
+                               (int64_t)0, (int64_t)0));
       RHQR_LAUNCH_CHECK();
     } else {
       int nb = (int)ceil_div(n, LG_RB);
@@ -248,7 +260,8 @@ static rhqr_status left_typed(const SketchView &s, const T *W, int64_t n, int32_
                                                                              scale, y);
       RHQR_LAUNCH_CHECK();
     }
-    left_rhvector_kernel<T><<<1, 256, 0, st>>>(y, p, m, j, scaling, S, lds, R, beta, gam, U, ldu, info, stop);
+    RHQR_CUDA_TRY(launch_pdl(left_rhvector_kernel<T>, dim3(1), dim3(256), 0, st, (const double *)y, p, m, j, scaling,
+                             S, lds, R, beta, gam, U, ldu, info, stop, RhvBatch{}));
     RHQR_LAUNCH_CHECK();
   }
   // finish T's last column and the last column's scale
