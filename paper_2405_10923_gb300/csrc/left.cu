@@ -519,6 +519,8 @@ rhqr_status block_factor(const SketchView &s, const void *W, int32_t wt, int64_t
 // block per process.
 __global__ void arnoldi_coef_kernel(const double *T, int32_t M, const double *S, int64_t lds, int32_t j,
                                     const double *gamma, double *coef, int64_t bs_S) {
+  pdl_wait();
+  pdl_release();
   const int64_t b = blockIdx.x;
   T += b * (int64_t)M * M;
   S += b * bs_S;
@@ -552,6 +554,66 @@ __global__ void arnoldi_q_kernel(const T *U, int64_t ldu, int64_t n, int32_t j, 
   double acc = (i == j) ? 1.0 : 0.0;
   for (int l = 0; l <= j; ++l) acc -= (double)U[(int64_t)l * ldu + i] * c_s[l];
   q[i] = (T)acc;
+}
+
+// Vector form for 16-byte aligned U and q (float32 basis): each thread takes
+// V = 16 / sizeof(T) consecutive rows with one 16-byte load per column, four
+// independent chains in the basis precision (as the column refresh); the last
+// n % V rows go one at a time.
+template <class T>
+__global__ void __launch_bounds__(256) arnoldi_q_vec_kernel(const T *U, int64_t ldu, int64_t n, int32_t j,
+                                                            const double *coef, T *q, int64_t bs_U, int32_t M) {
+  pdl_wait();
+  using VT = typename Vec16<T>::type;
+  constexpr int V = Vec16<T>::V;
+  const int64_t b = blockIdx.y;
+  U += b * bs_U;
+  coef += b * M;
+  q += b * n;
+  __shared__ T c_s[1024];
+  for (int l = threadIdx.x; l <= j; l += blockDim.x) c_s[l] = (T)coef[l];
+  __syncthreads();
+  const int64_t nvec = n / V;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec + (n % V != 0);
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = v * V;
+    if (v < nvec) {
+      T p[4][V];
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int e = 0; e < V; ++e) p[t][e] = T(0);
+      const T *up = U + i0;
+      int l = 0;
+      for (; l + 4 <= j + 1; l += 4) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const VT u = *reinterpret_cast<const VT *>(up + t * ldu);
+          const T *ue = reinterpret_cast<const T *>(&u);
+#pragma unroll
+          for (int e = 0; e < V; ++e) p[t][e] += ue[e] * c_s[l + t];
+        }
+        up += 4 * ldu;
+      }
+      for (; l <= j; ++l, up += ldu) {
+        const VT u = *reinterpret_cast<const VT *>(up);
+        const T *ue = reinterpret_cast<const T *>(&u);
+#pragma unroll
+        for (int e = 0; e < V; ++e) p[l & 3][e] += ue[e] * c_s[l];
+      }
+      VT out;
+      T *oe = reinterpret_cast<T *>(&out);
+#pragma unroll
+      for (int e = 0; e < V; ++e) oe[e] = (i0 + e == j ? T(1) : T(0)) - ((p[0][e] + p[1][e]) + (p[2][e] + p[3][e]));
+      *reinterpret_cast<VT *>(q + i0) = out;
+    } else {
+      for (int64_t i = i0; i < n; ++i) {
+        T ps[4] = {T(0), T(0), T(0), T(0)};
+        for (int l = 0; l <= j; ++l) ps[l & 3] += U[(int64_t)l * ldu + i] * c_s[l];
+        q[i] = (i == j ? T(1) : T(0)) - ((ps[0] + ps[1]) + (ps[2] + ps[3]));
+      }
+    }
+  }
 }
 
 static int64_t arnoldi_stage_elems(const SketchView &s, int64_t n) {
@@ -605,9 +667,12 @@ static rhqr_status arnoldi_tcol(ArnoldiState &a, cudaStream_t st) {
   const int32_t J = a.j, M = a.M, B = a.nrhs;
   const int64_t p = (int64_t)a.view.k + M;
   dim3 g((unsigned)std::max(1, J), 2, (unsigned)B);
-  left_dots_kernel<<<g, 256, 0, st>>>(a.S, a.lds, p, J, J, a.z, 0, a.d, a.v, 0, a.lds * M, p, M);
+  RHQR_CUDA_TRY(launch_pdl(left_dots_kernel, g, dim3(256), 0, st, (const double *)a.S, a.lds, p, J, J,
+                           (const double *)a.z, 0, a.d, a.v, 0, a.lds * M, p, (int64_t)M));
   RHQR_LAUNCH_CHECK();
-  left_tcol_coef_kernel<<<(unsigned)B, 1024, 0, st>>>(a.T, M, J, a.beta, a.d, a.v, 0, a.c, 0, (int64_t)M * M, M);
+  RHQR_CUDA_TRY(launch_pdl(left_tcol_coef_kernel, dim3((unsigned)B), dim3(1024), 0, st, a.T, M, J,
+                           (const double *)a.beta, (const double *)a.d, (const double *)a.v, 0, a.c, 0,
+                           (int64_t)M * M, (int64_t)M));
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }
@@ -626,9 +691,9 @@ static rhqr_status arnoldi_reflect(ArnoldiState &a, const T *w, double *h, rhqr_
   if (a.view.kind == RHQR_SKETCH_SRHT) {
     RHQR_TRY(launch_refresh<T>(ca, (unsigned)B, st));
     RHQR_TRY(column_srht<T>(ca, a.view, (T *)a.stage, (unsigned)B, st));
-    left_srht_combine_kernel<T><<<dim3((unsigned)ceil_div(a.view.k, 8), (unsigned)B), 256, 0, st>>>(
-        (const T *)a.stage, a.view.N1, a.view.d2, a.view.sample_i1, a.view.sample_slot, a.view.k, M, scale, a.y,
-        a.stage_elems, p);
+    RHQR_CUDA_TRY(launch_pdl(left_srht_combine_kernel<T>, dim3((unsigned)ceil_div(a.view.k, 8), (unsigned)B),
+                             dim3(256), 0, st, (const T *)a.stage, a.view.N1, a.view.d2, a.view.sample_i1,
+                             a.view.sample_slot, a.view.k, M, scale, a.y, a.stage_elems, p));
     RHQR_LAUNCH_CHECK();
   } else {
     const dim3 gg((unsigned)ceil_div(a.n, LG_RB), (unsigned)B);
@@ -657,8 +722,9 @@ static rhqr_status arnoldi_reflect(ArnoldiState &a, const T *w, double *h, rhqr_
   }
   // RHVector at column J; its "R column" is the Hessenberg column h (M entries per process)
   RhvBatch bb{p, a.lds * M, M, M, a.ldu * M, 4};
-  left_rhvector_kernel<T><<<(unsigned)B, 256, 0, st>>>(a.y, p, M, J, a.scaling, a.S, a.lds, h - (int64_t)J * M,
-                                                       a.beta, a.gamma, (T *)a.U, a.ldu, info, a.stop, bb);
+  RHQR_CUDA_TRY(launch_pdl(left_rhvector_kernel<T>, dim3((unsigned)B), dim3(256), 0, st, (const double *)a.y, p, M, J,
+                           a.scaling, a.S, a.lds, h - (int64_t)J * M, a.beta, a.gamma, (T *)a.U, a.ldu, info, a.stop,
+                           bb));
   RHQR_LAUNCH_CHECK();
   RHQR_TRY(arnoldi_tcol(a, st));
   a.j = J + 1;
@@ -669,10 +735,24 @@ static rhqr_status arnoldi_reflect(ArnoldiState &a, const T *w, double *h, rhqr_
 template <class T>
 static rhqr_status arnoldi_basis(ArnoldiState &a, T *q, cudaStream_t st) {
   const int32_t J = a.j - 1, B = a.nrhs;
-  arnoldi_coef_kernel<<<(unsigned)B, 1024, 0, st>>>(a.T, a.M, a.S, a.lds, J, a.gamma, a.coef, a.lds * a.M);
+  RHQR_CUDA_TRY(launch_pdl(arnoldi_coef_kernel, dim3((unsigned)B), dim3(1024), 0, st, (const double *)a.T, a.M,
+                           (const double *)a.S, a.lds, J, (const double *)a.gamma, a.coef, a.lds * a.M));
   RHQR_LAUNCH_CHECK();
-  arnoldi_q_kernel<T><<<dim3((unsigned)ceil_div(a.n, 256), (unsigned)B), 256, 0, st>>>(
-      (const T *)a.U, a.ldu, a.n, J, a.coef, q, a.ldu * a.M, a.M);
+  // float32 basis: the vector kernel (its float64 form would stay bound by the
+  // FP64 rate, so the float64 basis keeps the one-chain float64 sum)
+  constexpr int V = Vec16<T>::V;
+  const bool aligned = a.ldu % V == 0 && ((uintptr_t)a.U % 16) == 0 && ((uintptr_t)q % 16) == 0 &&
+                       (B == 1 || a.n % V == 0);
+  if (sizeof(T) == 4 && aligned) {
+    const int64_t units = ceil_div(a.n, V);
+    const dim3 g((unsigned)std::min<int64_t>(ceil_div(units, 256), std::max<int64_t>(1, 152 * 8 / (int64_t)B)),
+                 (unsigned)B);
+    RHQR_CUDA_TRY(launch_pdl(arnoldi_q_vec_kernel<T>, g, dim3(256), 0, st, (const T *)a.U, a.ldu, a.n, J,
+                             (const double *)a.coef, q, a.ldu * a.M, a.M));
+  } else {
+    arnoldi_q_kernel<T><<<dim3((unsigned)ceil_div(a.n, 256), (unsigned)B), 256, 0, st>>>(
+        (const T *)a.U, a.ldu, a.n, J, a.coef, q, a.ldu * a.M, a.M);
+  }
   RHQR_LAUNCH_CHECK();
   return RHQR_OK;
 }
@@ -696,9 +776,12 @@ static rhqr_status arnoldi_step_t(ArnoldiState &a, const T *w, double *h, T *qn,
   RHQR_TRY(sketch_apply_simt(a.view, M, w, sizeof(T) == 8 ? RHQR_F64 : RHQR_F32, a.n, B, a.n, a.z, p, a.aws,
                              a.aws_bytes, st));
   dim3 g((unsigned)J, 2, (unsigned)B);
-  left_dots_kernel<<<g, 256, 0, st>>>(a.S, a.lds, p, 0, 0, a.z, J, a.d, a.v, 0, a.lds * M, p, M);
+  RHQR_CUDA_TRY(launch_pdl(left_dots_kernel, g, dim3(256), 0, st, (const double *)a.S, a.lds, p, 0, 0,
+                           (const double *)a.z, J, a.d, a.v, 0, a.lds * M, p, (int64_t)M));
   RHQR_LAUNCH_CHECK();
-  left_tcol_coef_kernel<<<(unsigned)B, 1024, 0, st>>>(a.T, M, -1, a.beta, a.d, a.v, J, a.c, 0, (int64_t)M * M, M);
+  RHQR_CUDA_TRY(launch_pdl(left_tcol_coef_kernel, dim3((unsigned)B), dim3(1024), 0, st, a.T, M, -1,
+                           (const double *)a.beta, (const double *)a.d, (const double *)a.v, J, a.c, 0,
+                           (int64_t)M * M, (int64_t)M));
   RHQR_LAUNCH_CHECK();
   RHQR_TRY(arnoldi_reflect<T>(a, w, h, info, st));
   if (qn != nullptr) RHQR_TRY(arnoldi_basis<T>(a, qn, st));
