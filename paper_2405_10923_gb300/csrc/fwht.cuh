@@ -18,6 +18,9 @@
 
 namespace rhqr {
 
+__device__ __forceinline__ float fwht_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fwht_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <class T, int LOGN2>
 __device__ __forceinline__ void fwht_segment(T (&v)[16], T *buf) {
   static_assert(LOGN2 >= 9 && LOGN2 <= 13, "segments of 512 .. 8192 entries");
@@ -34,14 +37,15 @@ __device__ __forceinline__ void fwht_segment(T (&v)[16], T *buf) {
         v[r] = a + b;
         v[r + h] = a - b;
       }
-  // lane bits
+  // lane bits: the upper lane of a pair keeps u - v, the lower v + u, both as
+  // one fma(sign, v, u) (exact product by +-1, one rounding: the same value)
 #pragma unroll
   for (int s = 1; s < 32; s <<= 1) {
-    const bool upper = (lane & s) != 0;
+    const T sgn = (lane & s) != 0 ? T(-1) : T(1);
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const T u = __shfl_xor_sync(0xffffffffu, v[r], s);
-      v[r] = upper ? u - v[r] : v[r] + u;
+      v[r] = fwht_fma(sgn, v[r], u);
     }
   }
 #pragma unroll
