@@ -10,9 +10,10 @@
 // last, so the float32 accumulator only holds A F -- small next to Y in
 // refinement passes, where Tri is close to a signed identity -- until A itself
 // arrives.  Six limb products (weight >= 2^-16) are taken when F is not small,
-// with the big one in a second accumulator added in float32 by the epilogue;
 // three (plus A's smallest limb through the diagonal) when F is small enough
-// that the dropped ones stay below float32 rounding.
+// that the dropped ones stay below float32 rounding; either way into one
+// float32 accumulator per buffer, so the accumulators are double-buffered and
+// the epilogue of a tile overlaps the MMAs of the next.
 //
 // Tiles of 128 rows.  Columns are grouped in chunks of 64; row chunk kc of
 // (I + F) feeds the column chunks c >= kc, one MMA group per row chunk.  For
@@ -21,7 +22,7 @@
 // for three); each CTA keeps its blocks of (I + F) in shared memory as B
 // operands.  Tensor memory per CTA: two A stages (one 64-column chunk, three
 // limbs x 32 columns) and two accumulators of up to 128 columns (a double
-// buffer, or the pair of the six-product case).  For an in-place solve a CTA
+// buffer).  For an in-place solve a CTA
 // stores its columns of a tile only after the peer CTA's loaders have read the
 // tile (counters in its shared memory that the peer increments).
 //
@@ -140,8 +141,8 @@ __device__ __forceinline__ int choose_nprod(int forced, int m, float fmax) {
 //   NPROD 3: (1,0) (0,1) (0,0)          [A limb, (I + F) limb]
 //   NPROD 4: (2,0) (1,0) (0,1) (0,0)    (the group holds a diagonal block: all
 //                                        three limbs of A pass through the identity)
-//   NPROD 6: (2,0) (1,1) (0,2) (1,0) (0,1) | (0,0) into the second accumulator
-template <int NPROD, bool TWO>
+//   NPROD 6: (2,0) (1,1) (0,2) (1,0) (0,1) (0,0)
+template <int NPROD>
 __device__ __forceinline__ void issue_group(uint32_t dcol, uint32_t a_stage, uint32_t dhi, uint32_t blo,
                                             uint32_t lstride, uint32_t idesc, bool first) {
   constexpr int PA3[3] = {1, 0, 0}, PB3[3] = {0, 1, 0};
@@ -151,14 +152,12 @@ __device__ __forceinline__ void issue_group(uint32_t dcol, uint32_t a_stage, uin
   for (int pr = 0; pr < NPROD; ++pr) {
     const int pa = NPROD == 3 ? PA3[pr] : NPROD == 4 ? PA4[pr] : PA6[pr];
     const int pb = NPROD == 3 ? PB3[pr] : NPROD == 4 ? PB4[pr] : PB6[pr];
-    const bool big = TWO && pr == NPROD - 1;
-    const uint32_t d = dcol + (big ? (uint32_t)MAX_W : 0u);
     const uint32_t lo = blo + (uint32_t)pb * lstride;
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
       // the first MMA into an accumulator of row chunk 0 starts the sums
-      const uint32_t accumulate = (!first || kk > 0 || (pr > 0 && !big)) ? 1u : 0u;
-      tc::mma_ts(d, a_stage + (uint32_t)(pa * 32 + kk * 8), ((uint64_t)dhi << 32) | (lo + 2u * kk), idesc,
+      const uint32_t accumulate = (!first || kk > 0 || pr > 0) ? 1u : 0u;
+      tc::mma_ts(dcol, a_stage + (uint32_t)(pa * 32 + kk * 8), ((uint64_t)dhi << 32) | (lo + 2u * kk), idesc,
                  accumulate);
     }
   }
@@ -273,15 +272,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   const int64_t t0 = P.split ? (int64_t)(blockIdx.x >> 1) : (int64_t)blockIdx.x;
   const int64_t tstep = P.split ? (int64_t)(gridDim.x >> 1) : (int64_t)gridDim.x;
 
-  // Six products (F not small, e.g. the first pass of an ill-conditioned W):
-  // the big product A0 F0 and A0 through the identity go to one accumulator,
-  // the smaller products to a second one, summed in float32 by the epilogue,
-  // so that few tensor-core roundings act at the scale of the partial sums;
-  // one accumulator pair per CTA (the epilogue drains a tile before the next
-  // starts).  Three products: one accumulator, double-buffered.
+  // Six products when F is not small (e.g. the first pass of an
+  // ill-conditioned W), three otherwise; one accumulator, double-buffered.
   const int nprod = choose_nprod(P.nprod, m, __uint_as_float(*fmax_s));
-  const bool two = nprod == 6;
-  const uint32_t nbuf = two ? 1u : 2u;
+  constexpr uint32_t nbuf = 2;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -311,19 +305,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const uint32_t blo = bsm_lo + (uint32_t)(G.boff >> 4), lstride = (uint32_t)G.N * 8u;
           const uint32_t idesc = tc::idesc_bf16(128, G.N);
           const bool first = G.kc == 0;
-          if (two) issue_group<6, true>(dcol, a_stage, dhi, blo, lstride, idesc, first);
-          else if (G.diag) issue_group<4, false>(dcol, a_stage, dhi, blo, lstride, idesc, first);
-          else issue_group<3, false>(dcol, a_stage, dhi, blo, lstride, idesc, first);
+          if (nprod == 6) issue_group<6>(dcol, a_stage, dhi, blo, lstride, idesc, first);
+          else if (G.diag) issue_group<4>(dcol, a_stage, dhi, blo, lstride, idesc, first);
+          else issue_group<3>(dcol, a_stage, dhi, blo, lstride, idesc, first);
           tc::mma_commit(a_empty + s);
-          // one accumulator buffer (six products): an owned chunk is complete
-          // after its diagonal group, and the epilogue drains it while the later
-          // groups run; two buffers: the tile is handed over whole
-          if (nbuf == 1)
-            for (int ci = 0; ci < C.ncc; ++ci)
-              if (C.cc[ci] == kc) tc::mma_commit(acc_full + 2 * b + ci);
         }
         if (!ok) break;
-        if (nbuf == 2) tc::mma_commit(acc_full + 2 * b);
+        // the tile is handed over whole (the next tile's MMAs use the other buffer)
+        tc::mma_commit(acc_full + 2 * b);
       }
       tc::mma_quiesce(mma_done);  // no MMA in flight when tensor memory is released
     }
@@ -439,13 +428,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int64_t row = t * TILE + r;
       const bool live = row < P.nrows;
       const bool issuer = qd == 0 && lane == 0;  // the epilogue thread that issues TMA stores
-      // owned chunks in the order the MMA thread completes them; each one's
-      // accumulator columns are released as soon as they have been read
+      // the owned chunks of the tile (one commit for the whole tile); each
+      // one's accumulator columns are released as soon as they have been read
       for (int ci = 0; ci < C.ncc; ++ci) {
-        // two accumulator buffers: one commit for the whole tile (the next
-        // tile's MMAs do not wait for this drain)
         bool okw = true;
-        if (nbuf == 1 || ci == 0) okw = tc::mbar_wait(acc_full + 2 * b + (nbuf == 1 ? ci : 0), u & 1u, P.budget, err_s, abort_s);
+        if (ci == 0) okw = tc::mbar_wait(acc_full + 2 * b, u & 1u, P.budget, err_s, abort_s);
         okw = __all_sync(0xffffffffu, okw);
         // the four epilogue warps share named barriers: they stop together
         if (P.use_tma_y) okw = tc::named_and(1, 128, okw);
@@ -487,14 +474,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             for (int h = 0; h < wc / 16; ++h) {
               const uint32_t col =
                   tmem + lane_base + (uint32_t)(ACC_COL0 + b * MAX_W + C.cc_acc[ci] + c0 + 16 * h);
-              uint32_t a0[16], b0[16];
+              uint32_t a0[16];
               tc::tmem_ld16(col, a0);
-              if (two) tc::tmem_ld16(col + (uint32_t)MAX_W, b0);
               tc::tmem_wait_ld();
 #pragma unroll
-              for (int j = 0; j < 16; ++j)
-                yb[(16 * h + j) * TILE + r] =
-                    two ? __uint_as_float(a0[j]) + __uint_as_float(b0[j]) : __uint_as_float(a0[j]);
+              for (int j = 0; j < 16; ++j) yb[(16 * h + j) * TILE + r] = __uint_as_float(a0[j]);
             }
             tc::fence_proxy_async();
             tc::named_sync(1, 128);
@@ -507,16 +491,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         } else {
           for (int cb = 0; cb < C.cc_w[ci] / 16; ++cb) {
             const uint32_t col = tmem + lane_base + (uint32_t)(ACC_COL0 + b * MAX_W + C.cc_acc[ci] + cb * 16);
-            uint32_t a0[16], b0[16];
+            uint32_t a0[16];
             tc::tmem_ld16(col, a0);
-            if (two) tc::tmem_ld16(col + (uint32_t)MAX_W, b0);
             tc::tmem_wait_ld();
             if (live) {
               const int col0 = C.cc[ci] * 64 + cb * 16;
               float *y = P.Y + (int64_t)col0 * P.ldy + row;
 #pragma unroll
               for (int j = 0; j < 16; ++j) {
-                const float v = two ? __uint_as_float(a0[j]) + __uint_as_float(b0[j]) : __uint_as_float(a0[j]);
+                const float v = __uint_as_float(a0[j]);
                 if (col0 + j < m) y[(int64_t)j * P.ldy] = v;
               }
             }
