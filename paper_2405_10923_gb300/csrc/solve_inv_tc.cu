@@ -104,7 +104,6 @@ struct Params {
   int32_t m, nprod, split, bregion;  // nprod: 6, 3, or 0 = chosen from max |F|
   int32_t use_tma;                   // X staged by TMA (16-byte aligned X and ld), else column loads
   int32_t use_tma_y;                 // Q written by TMA stores from shared memory, else column stores
-  int32_t inplace;                   // Y == X: a tile is stored only after both CTAs have read it
   const double *Rinv;
   CtaPlan plan[2];
   rhqr_info *info;
@@ -441,7 +440,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           break;
         }
         tc::fence_after();
-        if (ci == 0 && P.split && P.inplace) {  // the peer's loaders must be done with this tile
+        // the peer's loaders must be done with this tile: in place, before it is
+        // overwritten; otherwise it keeps the pair within a tile of each other,
+        // so both CTAs read each X tile from L2 (without it the first,
+        // not-in-place pass read 1.66x the algorithmic bytes from DRAM)
+        if (ci == 0 && P.split) {
           const uint32_t need = 128u * (uint32_t)(it + 1);
           long long spins = 0;
           bool ok = true;
@@ -611,7 +614,6 @@ rhqr_status rows_solve_inv_tc(const float *X, int64_t ldx, int64_t nrows, int32_
   P.Rinv = Rinv;
   P.info = info;
   P.budget = budget;
-  P.inplace = X == Y ? 1 : 0;
   CUtensorMap mapX;
   std::memset(&mapX, 0, sizeof(mapX));
   P.use_tma = 0;
