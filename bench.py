@@ -40,7 +40,7 @@ REF_ROWS = 4096  # rows per step of the reference arm (about 4 s of CPU work eac
 # DRAM bytes (read + write) per launch at n = 2^22, m = 256, k = 1024, from ncu
 # captures at n = 2^20 scaled by 4 (both kernels stream W / Q and the operator in
 # proportion to n); None when the kernel changed since the counters were taken.
-TRAFFIC_BYTES = {"sketch": 4 * (3.3153e9 + 4.95e6), "solve": 4 * (1.0742e9 + 1.0212e9), "hqr": None}
+TRAFFIC_BYTES = {"sketch": 4 * (3.2899e9 + 4.86e6), "solve": 4 * (1.0773e9 + 1.0140e9), "hqr": None}
 
 
 def parse_args():
