@@ -53,3 +53,14 @@ def test_argument_errors_are_synchronous():
     assert rh.load().rhqr_pipeline_destroy(None) == 0
     # GMRES solution: null handles and buffers are rejected on the host
     assert rh.load().rhqr_arnoldi_solution(None, None, 0, 1, None, None, None, None, None, None) == 1
+
+
+def test_last_cuda_error_query_without_a_gpu():
+    """rhqr_last_cuda_error is 0 until a call returns RHQR_ECUDA, and
+    rhqr_cuda_error_name gives the CUDA runtime's name for a code (host only)."""
+    import paper_2405_10923_gb300 as rh
+
+    lib = rh.load()
+    code, name = rh.rhqr_last_cuda_error()
+    assert code == 0 and name == "cudaSuccess"
+    assert lib.rhqr_cuda_error_name(912).decode() == "cudaErrorInvalidClusterSize"
